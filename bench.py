@@ -1,0 +1,308 @@
+"""Benchmark of the Chung-Lu generator on GB300 (one JSON line on stdout).
+
+Default workload: the paper's power-law shape at one-GPU scale -- n = 10^8
+nodes, integer degrees drawn from P(d) ~ d^-2.3 on [20, 10^5] (degree seed 3,
+sorted non-increasing), edge seed 42, int32 (u, v) output (~3.9e9 edges,
+~31 GB).  One step = the whole hot path on device-resident weights:
+cl_plan_create (validation, exact S, item space), cl_plan_build (costs, cost
+prefix, Eq. 3 tasks), cl_count, cl_scan (reads m back), cl_emit.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain single-threaded restatement
+of Algorithm 1) on a bounded sample of the same workload.  Under torchrun
+each rank generates an independent graph (seed 42 + rank): weak scaling, no
+data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges/sec on 1 GB300 and % of HBM write roofline; batched graphs/sec; calibrate s"
+WORKLOAD = "pl_n1e8"
+CONFIG = {"workload": "chung-lu power law n=1e8, gamma=2.3, degrees [20,1e5], degree seed 3, edge seed 42, "
+                      "int32 edge pairs", "n": 100_000_000, "gamma": 2.3, "dmin": 20, "dmax": 100_000,
+          "heavy_w": 8192.0, "segment": 65536, "etype": "int32 pairs",
+          "l2": "inputs (400 MB weights) and outputs (~31 GB edges) exceed the 129 MB L2; no flush needed"}
+KERNELS_PER_STEP = 14  # analyze 1 + weight prefix 3 + costs/scan/tasks 5 + count 1 + count scan 3 + emit 1
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = open(os.path.join("/tmp", f"clocks_{os.getpid()}.csv"), "w+")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        self.f.close()
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w: np.ndarray, seed: int, budget_s: float = 15.0):
+    """The oracle as it stands, single-threaded, on random item ranges of the
+    same workload until the time budget is spent."""
+    import oracle
+
+    g = oracle.Graph(w, seed)
+    rng = np.random.default_rng(12345)
+    edges, spent, items, nr = 0, 0.0, 0, 0
+    while spent < budget_s:
+        a = int(rng.integers(0, g.n_items - 2000))
+        t0 = time.perf_counter()
+        c = g.count_items(a, a + 2000)
+        spent += time.perf_counter() - t0
+        edges += int(c.sum())
+        items += 2000
+        nr += 1
+    return {"value": edges / spent, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"{nr} random ranges of 2000 consecutive items ({items} items, {edges} edges) of the same "
+                      f"workload, count pass of the single-threaded oracle, {spent:.1f} s"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    from paper_1406_1215_gb300 import inputs
+
+    w, seed = inputs.workload(WORKLOAD)
+    per_step = []
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, seed, budget_s=4.0)
+        if s >= args.warmup:
+            per_step.append(cb["value"])
+    v = statistics.mean(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/binary128", "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: random ranges of 2000 items of the workload, ~4 s of CPU"},
+            "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1406_1215_gb300 as P
+    from paper_1406_1215_gb300 import inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    w_np, seed = inputs.workload(WORKLOAD)
+    seed = seed + rank
+    n = len(w_np)
+    w = torch.from_numpy(w_np).to(dev)
+    graph = P.cl_graph(n, P.CL_W_I32, w.data_ptr(), seed, 8192.0)
+    sb = P.cl_plan_scratch_bytes(1)
+    scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+
+    # sizes from one untimed pass
+    plan = P.cl_plan_create([graph], None, scratch, sb, sh)
+    wb = P.cl_plan_workspace_bytes(plan)
+    ws = torch.empty(wb, dtype=torch.uint8, device=dev)
+    P.cl_plan_build(plan, ws, wb, sh)
+    n_items = P.cl_plan_items(plan)
+    counts = torch.empty(n_items, dtype=torch.int32, device=dev)
+    offsets = torch.empty(n_items + 1, dtype=torch.int64, device=dev)
+    P.cl_count(plan, counts, sh)
+    m = P.cl_scan(plan, counts, offsets, True, sh)
+    P.cl_plan_destroy(plan)
+    cap = int(m * 1.0005) + 1024
+    edges = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    kern = {"count": [], "emit": []}
+
+    def step(timed_kernels: bool):
+        pl = P.cl_plan_create([graph], None, scratch, sb, sh)
+        P.cl_plan_build(pl, ws, wb, sh)
+        e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+        e0.record(stream)
+        P.cl_count(pl, counts, sh)
+        e1.record(stream)
+        mm = P.cl_scan(pl, counts, offsets, True, sh)
+        e2.record(stream)
+        P.cl_emit(pl, offsets, P.CL_E_I32, edges, cap, 0, n_items, sh)
+        e3.record(stream)
+        if timed_kernels:
+            kern["count"].append((e0, e1))
+            kern["emit"].append((e2, e3))
+        err = P.cl_check(pl, sh)
+        P.cl_plan_destroy(pl)
+        if err != 0:
+            raise RuntimeError(f"device error {err}")
+        return mm
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    t0, t1 = ev(), ev()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    ms = []
+    for _ in range(args.steps):
+        ms.append(step(True))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    if dist:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+        mt = torch.tensor([float(sum(ms))], device=dev, dtype=torch.float64)
+        dist.all_reduce(mt)
+        total_edges = float(mt.item())
+    else:
+        total_edges = float(sum(ms))
+    value = total_edges / elapsed
+    t_emit = statistics.mean(a.elapsed_time(b) for a, b in kern["emit"]) / 1e3
+    t_count = statistics.mean(a.elapsed_time(b) for a, b in kern["count"]) / 1e3
+    m_step = ms[-1]
+    peak, how = peaks()
+    achieved = 8.0 * m_step / t_emit / 1e9
+
+    # end to end: weights from pinned host memory, edge list back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        w_host = torch.from_numpy(w_np).pin_memory()
+        out_host = torch.empty((cap, 2), dtype=torch.int32, pin_memory=True)
+        w_dev = torch.empty_like(w)
+        graph2 = P.cl_graph(n, P.CL_W_I32, w_dev.data_ptr(), seed, 8192.0)
+        e_steps = max(1, min(args.steps, 3))
+
+        def e2e_step():
+            w_dev.copy_(w_host, non_blocking=True)
+            pl = P.cl_plan_create([graph2], None, scratch, sb, sh)
+            P.cl_plan_build(pl, ws, wb, sh)
+            P.cl_count(pl, counts, sh)
+            mm = P.cl_scan(pl, counts, offsets, True, sh)
+            P.cl_emit(pl, offsets, P.CL_E_I32, edges, cap, 0, n_items, sh)
+            out_host[:mm].copy_(edges[:mm], non_blocking=True)
+            P.cl_plan_destroy(pl)
+            return mm
+
+        e2e_step()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        em = [e2e_step() for _ in range(e_steps)]
+        b.record(stream)
+        torch.cuda.synchronize()
+        et = a.elapsed_time(b) / 1e3
+        e2e = {"value": sum(em) / et, "unit": "edges/s", "h2d_bytes_per_step": 4 * n,
+               "d2h_bytes_per_step": 8 * em[-1], "steps": e_steps}
+        del out_host, w_host
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32x2", "data": "synthetic", "config": CONFIG,
+        "edges_per_step": m_step,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "sample_kernel<emit,int2>", "peak_source": how,
+                     "algorithmic_bytes": "8 B per edge written (int32 pair)"},
+        "kernel_ms": {"count": t_count * 1e3, "emit": t_emit * 1e3},
+        "hbm_write_frac_step": 8.0 * m_step / (elapsed / args.steps) / 1e9 / peak,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+    }
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w_np, seed)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * cl.h -- C ABI of a single-GPU (GB300, sm_103a) Chung-Lu random-network
+ * generator: the edge-skipping sampler of Algorithm 1 of Alam & Khan,
+ * "Parallel Algorithms for Generating Random Networks with Given Degree
+ * Sequences" (Section 3), parallelised over source nodes with the paper's
+ * cost model (Eq. 1, Eq. 2, Eq. 6) and uniform cost partitioning (Eq. 3,
+ * Algorithm 2), plus capped expected degrees and their adjoint for weight
+ * calibration.
+ *
+ * Problem statement (Section 3): n nodes with non-negative weights
+ * w_0 >= w_1 >= ... >= w_{n-1} (sorted non-increasing), S = sum_k w_k; each
+ * pair (u, v), u < v, is an edge independently with probability
+ * min(w_u w_v / S, 1).  A weight sequence and a seed go in; an edge list
+ * (u, v), u < v, comes out, in canonical order (u ascending, then v
+ * ascending) -- exactly the order of Algorithm 1 run sequentially.
+ *
+ * Conventions for every call:
+ *   - pointers named d_* are CUDA device pointers owned by the caller; h_*
+ *     are host pointers owned by the caller.  The library never allocates
+ *     device memory: scratch and workspace are caller-provided.
+ *   - calls are asynchronous on `stream` unless documented as synchronizing.
+ *   - every call returns a cl_status; device-side consistency failures are
+ *     recorded in a device error word and reported by the next synchronizing
+ *     call (cl_check, cl_stats, cl_scan with a non-null h_total).  No kernel
+ *     traps, asserts or waits on another block.
+ *   - vertex ids are positions in the sorted order; relabelling is the
+ *     caller's job.
+ *
+ * The random stream (fixes every output bit; independent of launch shape):
+ *   item    = a light row u (w_u < heavy_w): v in [u+1, n), segment field
+ *             0xFFFFFFFF; or a heavy row u (w_u >= heavy_w) cut at absolute
+ *             multiples of 2^16 of v: v in [max(u+1, k 2^16), min(n, (k+1) 2^16)),
+ *             segment field k.
+ *   draw t  = Philox4x32-10, key (seed_lo, seed_hi), counter (t, segment,
+ *             u_lo, u_hi); words 0-1 give the skip uniform, words 2-3 the
+ *             acceptance uniform, each r = (2k+1)/2^53 from the top 52 bits.
+ *   loop    = Algorithm 1 per item: p = Q_prev/S with Q(v) = min(w_u w_v, S);
+ *             delta = floor(ln r / ln(1 - p)) (the exact real floor; 0 when
+ *             p = 1); v = j + delta; stop when v leaves the item; accept iff
+ *             r_a * Q_prev < Q_v exactly; Q_prev <- Q_v; j <- v + 1; stop when
+ *             Q_prev = 0.
+ */
+#ifndef CL_H
+#define CL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cl_stream_t; /* a cudaStream_t; NULL is the legacy default stream */
+
+typedef enum {
+  CL_OK = 0,
+  CL_ERR_INVALID_ARG = 1, /* null pointer, bad enum, negative size, bad item range */
+  CL_ERR_UNSORTED = 2,    /* weights not non-increasing (Section 3 precondition) */
+  CL_ERR_NONFINITE = 3,   /* a weight is negative, NaN or infinite */
+  CL_ERR_RANGE = 4,       /* n >= 2^31 (int32 ids) or n >= 2^32, S >= 2^53, or size overflow */
+  CL_ERR_CAPACITY = 5,    /* the output buffer is smaller than the edge count */
+  CL_ERR_WORKSPACE = 6,   /* scratch or workspace smaller than required */
+  CL_ERR_TIMEOUT = 7,     /* reserved: no call of this library waits on the device */
+  CL_ERR_CUDA = 8,        /* a CUDA runtime call failed */
+  CL_ERR_STATE = 9,       /* call order violated (e.g. cl_count before cl_plan_build) */
+  CL_ERR_DEVICE = 10      /* a device-side consistency check failed (see cl_check) */
+} cl_status;
+
+typedef enum { CL_W_I32 = 0, CL_W_F64 = 1 } cl_wtype;
+typedef enum { CL_E_I32 = 0, CL_E_I64 = 1 } cl_etype;
+
+/* One Chung-Lu instance.  heavy_w and the segment width (2^16) are stream
+ * parameters: they change which random numbers are drawn, hence the output.
+ * For CL_W_I32 the weights are integers (expected degrees) and S must be
+ * < 2^53; for CL_W_F64 they are finite non-negative doubles. */
+typedef struct {
+  int64_t n;          /* nodes; n < 2^31 */
+  int32_t wtype;      /* cl_wtype */
+  const void* d_w;    /* device array of n weights, sorted non-increasing; read only */
+  uint64_t seed;      /* Philox key */
+  double heavy_w;     /* rows with w_u >= heavy_w are segmented (default 8192) */
+} cl_graph;
+
+/* Performance knobs only: no choice changes any output bit. */
+typedef struct {
+  int32_t tasks;         /* number of equal-cost tasks (Eq. 3 partitions); 0 = automatic */
+  int32_t block;         /* threads per block of the sampler kernels, multiple of 32; 0 = 256 */
+  int32_t blocks_per_sm; /* resident blocks per SM for the persistent sampler grid; 0 = automatic */
+} cl_tuning;
+
+typedef struct {
+  int64_t n, H;           /* nodes, heavy rows */
+  int64_t n_items;        /* items of this graph */
+  int64_t item_begin;     /* first global item index of this graph in the plan */
+  int64_t S_i64;          /* exact weight sum (CL_W_I32) */
+  double S;               /* weight sum as a double (CL_W_F64: correctly rounded) */
+  int32_t status;         /* cl_status of this graph's validation */
+} cl_graph_info;
+
+typedef struct {
+  int64_t iterations;     /* loop iterations (Philox blocks) of the last count pass */
+  int64_t fallbacks;      /* skips decided by the double-double tier (last count pass) */
+  int64_t ties;           /* skips within 2^-96 x of an integer (took the nearest integer) */
+  int32_t error;          /* device error word (0 = none) */
+} cl_run_stats;
+
+typedef struct cl_plan cl_plan; /* opaque host handle */
+
+const char* cl_status_string(cl_status s);
+
+/* --- planning (Section 4: the sum S, the cost model Eq. 1-2 / Eq. 6 and the
+ *     uniform cost partition Eq. 3 / Algorithm 2) ------------------------- */
+
+/* Bytes of device scratch cl_plan_create needs for G graphs. */
+size_t cl_plan_scratch_bytes(int32_t G);
+
+/* Validates every graph (sorted non-increasing, non-negative, finite), computes
+ * S = sum_k w_k exactly (Algorithm 1, first line; integer weights: exact int64
+ * sum; double weights: the correctly rounded value of the exact sum), the
+ * heavy rows and the item space.  SYNCHRONIZING (reads the results back).
+ * graphs: host array of G descriptors (copied; the device weight arrays must
+ * stay alive and unchanged for the plan's lifetime).  d_scratch: at least
+ * cl_plan_scratch_bytes(G) bytes, free again when the call returns.
+ * Errors: CL_ERR_INVALID_ARG, CL_ERR_RANGE, CL_ERR_UNSORTED, CL_ERR_NONFINITE
+ * (the first failing graph's status; per-graph status via cl_plan_graph_info),
+ * CL_ERR_WORKSPACE, CL_ERR_CUDA.  On error *out is NULL. */
+cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tuning, void* d_scratch,
+                         size_t scratch_bytes, cl_stream_t stream, cl_plan** out);
+
+/* Device workspace bytes cl_plan_build needs (cost prefix, task table, scan
+ * partials, counters). */
+cl_status cl_plan_workspace_bytes(const cl_plan* plan, size_t* bytes);
+
+/* Builds the equal-cost task split of Eq. 3 in the workspace: per item
+ * c = 1 + (w_u / S) * sum_{v in item} w_v (Eq. 1-2; Eq. 6 for light rows),
+ * C = inclusive prefix of c (Calc-Cost of Algorithm 2 as a device-wide scan),
+ * task t starts at the first item with C >= t * Zbar, Zbar = C_total / tasks
+ * (Eq. 3; found as the items where floor(C / Zbar) changes, the rule of
+ * Find-Boundaries).  Asynchronous; capturable in a CUDA graph.  d_ws must stay
+ * reserved for the plan until cl_plan_destroy.  Tasks only schedule work: the
+ * output does not depend on them. */
+cl_status cl_plan_build(cl_plan* plan, void* d_ws, size_t ws_bytes, cl_stream_t stream);
+
+cl_status cl_plan_items(const cl_plan* plan, int64_t* n_items);
+cl_status cl_plan_graph_info(const cl_plan* plan, int32_t g, cl_graph_info* out);
+
+/* --- sampling (Algorithm 1, Create-Edges, per item) ---------------------- */
+
+/* Count pass: d_counts[i] = number of edges of global item i (int32, n_items
+ * entries, caller-owned).  Asynchronous. */
+cl_status cl_count(cl_plan* plan, int32_t* d_counts, cl_stream_t stream);
+
+/* Exclusive scan of the counts: d_offsets[i] = sum_{k<i} d_counts[k] for
+ * i = 0..n_items (n_items + 1 int64 entries; d_offsets[n_items] = m).  If
+ * h_total is non-null the call SYNCHRONIZES and writes m there, and reports a
+ * pending device error as CL_ERR_DEVICE.  d_counts and d_offsets must not
+ * overlap. */
+cl_status cl_scan(cl_plan* plan, const int32_t* d_counts, int64_t* d_offsets, int64_t* h_total,
+                  cl_stream_t stream);
+
+/* Emit pass: regenerates items [item_begin, item_end) and writes edge k of
+ * item i to d_edges[d_offsets[i] - d_offsets[item_begin] + k] as a (u, v)
+ * pair of etype (CL_E_I32: 2 x int32 = 8 bytes; CL_E_I64: 2 x int64 = 16
+ * bytes), u < v, local vertex ids of the item's graph.  capacity = edges that
+ * fit in d_edges; a range whose edges exceed it is not written and sets
+ * CL_ERR_CAPACITY in the device error word (the host cannot see m without a
+ * synchronisation).  Asynchronous.  d_offsets from cl_scan of the same plan. */
+cl_status cl_emit(cl_plan* plan, const int64_t* d_offsets, int32_t etype, void* d_edges, int64_t capacity,
+                  int64_t item_begin, int64_t item_end, cl_stream_t stream);
+
+/* Count + scan + emit for every graph of the plan, with no host round trip:
+ * graph g's edges start at d_graph_offsets[g] (G + 1 int64 entries,
+ * d_graph_offsets[G] = total edges) and carry the graph's local vertex ids.
+ * d_counts (n_items int32) and d_offsets (n_items + 1 int64) are caller
+ * scratch.  If the total exceeds capacity nothing is written to d_edges and
+ * *d_status (device int32) is set to CL_ERR_CAPACITY, else to CL_OK.
+ * Asynchronous; capturable in a CUDA graph (the batched path of a CUDA-graph
+ * replay).  Requires cl_plan_build. */
+cl_status cl_generate_batch(cl_plan* plan, int32_t etype, void* d_edges, int64_t capacity,
+                            int64_t* d_graph_offsets, int32_t* d_counts, int64_t* d_offsets,
+                            int32_t* d_status, cl_stream_t stream);
+
+/* SYNCHRONIZING: the run statistics of the last cl_count (flagged skips) and
+ * the device error word; resets the counters. */
+cl_status cl_stats(cl_plan* plan, cl_run_stats* out, cl_stream_t stream);
+
+/* SYNCHRONIZING: returns the device error word as a status and clears it. */
+cl_status cl_check(cl_plan* plan, cl_stream_t stream);
+
+void cl_plan_destroy(cl_plan* plan);
+
+/* --- diagnostics (exercise one primitive over arrays; for tests) ---------- */
+
+/* d_out[4i..4i+3] = Philox4x32-10(counter d_ctr[4i..4i+3], key (seed_lo, seed_hi)). */
+cl_status cl_diag_philox(const uint32_t* d_ctr, int64_t count, uint64_t seed, uint32_t* d_out,
+                         cl_stream_t stream);
+/* Same with NVIDIA cuRAND's device Philox4x32-10 (an independent implementation). */
+cl_status cl_diag_philox_curand(const uint32_t* d_ctr, int64_t count, uint64_t seed, uint32_t* d_out,
+                                cl_stream_t stream);
+/* -ln(A_i / B_i) for integers 1 <= A_i < B_i <= 2^55: d_ff[2i..2i+1] = float-float
+ * (hi, lo); d_dd[2i..2i+1] = double-double (hi, lo). */
+cl_status cl_diag_neglog(const uint64_t* d_A, const uint64_t* d_B, int64_t count, float* d_ff, double* d_dd,
+                         cl_stream_t stream);
+/* Skip of Algorithm 1 for r = (2 a_i + 1)/2^53, p = Q_i / S_i, remaining length R_i:
+ * d_delta[i] = min(floor(ln r / ln(1 - p)), R_i) (integer weights, 0 < Q_i < S_i < 2^53);
+ * d_tier[i] = 0 (float-float decided), 1 (double-double decided), 2 (tie: nearest integer). */
+cl_status cl_diag_skip(const uint64_t* d_a, const uint64_t* d_Q, const uint64_t* d_S, const int64_t* d_R,
+                       int64_t count, int64_t* d_delta, int32_t* d_tier, cl_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CL_H */

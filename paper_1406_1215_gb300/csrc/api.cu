@@ -1,0 +1,453 @@
+// api.cu -- the C ABI (include/cl.h): plan life cycle, count / scan / emit,
+// the batched path, statistics and error words.  Host code only; kernels live
+// in plan.cu and sample.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cl_internal.cuh"
+
+using namespace cl;
+
+struct cl_plan {
+  int G = 0;
+  int wtype = 0;
+  int device = 0;
+  int sms = 0;
+  std::vector<cl_graph> graphs;
+  std::vector<cl_graph_info> info;
+  std::vector<DevGraph> dg;
+  std::vector<long long> tile_begin;  // G + 1 prefix of weight-prefix tiles
+  long long ntiles = 0;
+  long long n_items = 0;
+  long long psize = 0;  // sum of (n_g + 1)
+  int T = 1;
+  int block = 256;
+  int grid_count = 0, grid_emit32 = 0, grid_emit64 = 0;
+  long long max_n = 0;
+  // workspace (after cl_plan_build)
+  bool built = false;
+  size_t ws_bytes = 0;
+  DevGraph* d_graphs = nullptr;
+  long long* d_tile_begin = nullptr;
+  double* d_P = nullptr;
+  double* d_C = nullptr;
+  double* d_part = nullptr;
+  long long* d_scan_part = nullptr;
+  long long* d_task = nullptr;
+  unsigned* d_ctr = nullptr;
+  int* d_err = nullptr;
+  unsigned long long* d_stats = nullptr;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <typename T>
+  T* take(size_t count) {
+    T* p = base ? (T*)(base + off) : nullptr;
+    off = align_up(off + count * sizeof(T));
+    return p;
+  }
+};
+
+cl_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? CL_OK : CL_ERR_CUDA; }
+cl_status last_ok() { return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA; }
+
+bool all_same_wtype(const cl_graph* g, int G) {
+  for (int i = 1; i < G; ++i)
+    if (g[i].wtype != g[0].wtype) return false;
+  return true;
+}
+
+// scratch of cl_plan_create
+struct ScratchLayout {
+  DevGraph* graphs;
+  long long* blk_begin;
+  double* heavy_w;
+  GraphAnalysis* res;
+  unsigned long long* bins;
+  size_t bytes;
+};
+
+ScratchLayout scratch_layout(void* base, int G, bool f64) {
+  Carver c(base);
+  ScratchLayout L;
+  L.graphs = c.take<DevGraph>(G);
+  L.blk_begin = c.take<long long>(G + 1);
+  L.heavy_w = c.take<double>(G);
+  L.res = c.take<GraphAnalysis>(G);
+  L.bins = f64 ? c.take<unsigned long long>(f64_bins_bytes(G) / sizeof(unsigned long long)) : nullptr;
+  L.bytes = c.off;
+  return L;
+}
+
+struct WsLayout {
+  DevGraph* graphs;
+  long long* tile_begin;
+  double* P;
+  double* C;
+  double* part;
+  long long* scan_part;
+  long long* task;
+  unsigned* ctr;
+  int* err;
+  unsigned long long* stats;
+  size_t bytes;
+};
+
+WsLayout ws_layout(void* base, const cl_plan* p) {
+  Carver c(base);
+  WsLayout L;
+  long long nt_items = scan_partials_needed(p->n_items);
+  long long nt = (p->ntiles > nt_items ? p->ntiles : nt_items) + 1;
+  L.graphs = c.take<DevGraph>(p->G);
+  L.tile_begin = c.take<long long>(p->G + 1);
+  L.P = c.take<double>(p->psize > 0 ? p->psize : 1);
+  L.C = c.take<double>(p->n_items > 0 ? p->n_items : 1);
+  L.part = c.take<double>(nt + (nt + 7) / 8);  // partials + one head byte per tile
+  L.scan_part = c.take<long long>(nt_items + 1);
+  L.task = c.take<long long>(p->T + 1);
+  L.ctr = c.take<unsigned>(4);
+  L.err = c.take<int>(4);
+  L.stats = c.take<unsigned long long>(4);
+  L.bytes = c.off;
+  return L;
+}
+
+DevPlan dev_plan(const cl_plan* p) {
+  DevPlan P;
+  P.graphs = p->d_graphs;
+  P.G = p->G;
+  P.n_items = p->n_items;
+  P.task_start = p->d_task;
+  P.T = p->T;
+  P.task_ctr = p->d_ctr;
+  P.err = p->d_err;
+  P.stats = p->d_stats;
+  return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cl_status_string(cl_status s) {
+  switch (s) {
+    case CL_OK: return "ok";
+    case CL_ERR_INVALID_ARG: return "invalid argument";
+    case CL_ERR_UNSORTED: return "weights are not sorted non-increasing";
+    case CL_ERR_NONFINITE: return "a weight is negative, NaN or infinite";
+    case CL_ERR_RANGE: return "size or value out of the supported range";
+    case CL_ERR_CAPACITY: return "output buffer too small";
+    case CL_ERR_WORKSPACE: return "scratch or workspace too small";
+    case CL_ERR_TIMEOUT: return "device wait expired";
+    case CL_ERR_CUDA: return "CUDA runtime error";
+    case CL_ERR_STATE: return "call order violated";
+    case CL_ERR_DEVICE: return "device-side consistency check failed";
+  }
+  return "unknown status";
+}
+
+size_t cl_plan_scratch_bytes(int32_t G) {
+  if (G <= 0) return 0;
+  return scratch_layout(nullptr, G, true).bytes;  // large enough for either weight type
+}
+
+cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tuning, void* d_scratch,
+                         size_t scratch_bytes, cl_stream_t stream, cl_plan** out) {
+  if (!out) return CL_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!graphs || G <= 0) return CL_ERR_INVALID_ARG;
+  if (!all_same_wtype(graphs, G)) return CL_ERR_INVALID_ARG;
+  const int wtype = graphs[0].wtype;
+  if (wtype != CL_W_I32 && wtype != CL_W_F64) return CL_ERR_INVALID_ARG;
+  for (int g = 0; g < G; ++g) {
+    if (graphs[g].n < 0) return CL_ERR_INVALID_ARG;
+    if (graphs[g].n > 0 && !graphs[g].d_w) return CL_ERR_INVALID_ARG;
+    if (graphs[g].n >= (1ll << 31)) return CL_ERR_RANGE;
+    if (std::isnan(graphs[g].heavy_w)) return CL_ERR_INVALID_ARG;
+  }
+  const bool f64 = wtype == CL_W_F64;
+  ScratchLayout SL = scratch_layout(d_scratch, G, f64);
+  if (!d_scratch || scratch_bytes < SL.bytes) return CL_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  cl_plan* p = new (std::nothrow) cl_plan();
+  if (!p) return CL_ERR_INVALID_ARG;
+  p->G = G;
+  p->wtype = wtype;
+  p->graphs.assign(graphs, graphs + G);
+  p->info.resize(G);
+  p->dg.resize(G);
+  cudaGetDevice(&p->device);
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+
+  // analysis: one block per 4096 weights of each graph
+  std::vector<long long> blk(G + 1, 0);
+  std::vector<double> hw(G);
+  for (int g = 0; g < G; ++g) {
+    DevGraph& d = p->dg[g];
+    std::memset(&d, 0, sizeof(d));
+    d.w = graphs[g].d_w;
+    d.n = graphs[g].n;
+    d.wtype = wtype;
+    d.key0 = (unsigned)graphs[g].seed;
+    d.key1 = (unsigned)(graphs[g].seed >> 32);
+    blk[g + 1] = blk[g] + (graphs[g].n + ANALYZE_CHUNK_HOST - 1) / ANALYZE_CHUNK_HOST;
+    hw[g] = graphs[g].heavy_w;
+  }
+  cl_status st = CL_OK;
+  std::vector<GraphAnalysis> res(G);
+  do {
+    if ((st = cuda_ok(cudaMemcpyAsync(SL.graphs, p->dg.data(), sizeof(DevGraph) * G, cudaMemcpyHostToDevice, s))))
+      break;
+    if ((st = cuda_ok(cudaMemcpyAsync(SL.blk_begin, blk.data(), sizeof(long long) * (G + 1), cudaMemcpyHostToDevice,
+                                      s))))
+      break;
+    if ((st = cuda_ok(cudaMemcpyAsync(SL.heavy_w, hw.data(), sizeof(double) * G, cudaMemcpyHostToDevice, s)))) break;
+    if ((st = cuda_ok(cudaMemsetAsync(SL.res, 0, sizeof(GraphAnalysis) * G, s)))) break;
+    if (f64 && (st = cuda_ok(cudaMemsetAsync(SL.bins, 0, f64_bins_bytes(G), s)))) break;
+    launch_analyze(SL.graphs, SL.blk_begin, G, blk[G], SL.heavy_w, SL.res, SL.bins, f64, s);
+    if (f64) launch_f64_sum_finalize(G, SL.bins, SL.res, s);
+    if ((st = last_ok())) break;
+    if ((st = cuda_ok(cudaMemcpyAsync(res.data(), SL.res, sizeof(GraphAnalysis) * G, cudaMemcpyDeviceToHost, s))))
+      break;
+    if ((st = cuda_ok(cudaStreamSynchronize(s)))) break;
+  } while (0);
+  if (st != CL_OK) {
+    delete p;
+    return st;
+  }
+
+  // item space and per-graph status
+  cl_status first_bad = CL_OK;
+  long long items = 0, pbase = 0;
+  p->tile_begin.assign(G + 1, 0);
+  for (int g = 0; g < G; ++g) {
+    DevGraph& d = p->dg[g];
+    cl_graph_info& I = p->info[g];
+    const long long n = graphs[g].n;
+    cl_status gs = CL_OK;
+    if (res[g].flags & 2u)
+      gs = CL_ERR_NONFINITE;
+    else if (res[g].flags & 1u)
+      gs = CL_ERR_UNSORTED;
+    if (f64) {
+      d.S_i = 0;
+      d.S_d = res[g].S_d;
+      if (gs == CL_OK && !std::isfinite(d.S_d)) gs = CL_ERR_NONFINITE;
+    } else {
+      d.S_i = (long long)res[g].S_i;
+      d.S_d = (double)d.S_i;
+      if (gs == CL_OK && res[g].S_i >= (1ull << 53)) gs = CL_ERR_RANGE;
+    }
+    d.H = (long long)res[g].H;
+    d.Hh = d.H < n - 1 ? d.H : (n > 0 ? n - 1 : 0);
+    d.n_heavy = d.Hh > 0 ? heavy_items_before(d.Hh, n) : 0;
+    long long light = n - 1 - d.H;
+    d.n_items = d.n_heavy + (light > 0 ? light : 0);
+    if (gs != CL_OK) d.n_items = 0, d.n_heavy = 0;
+    d.item_begin = items;
+    d.pbase = pbase;
+    items += d.n_items;
+    pbase += n + 1;
+    p->tile_begin[g + 1] = p->tile_begin[g] + (n + 1 + SCAN_TILE_HOST - 1) / SCAN_TILE_HOST;
+    if (n > p->max_n) p->max_n = n;
+    I.n = n;
+    I.H = d.H;
+    I.n_items = d.n_items;
+    I.item_begin = d.item_begin;
+    I.S_i64 = d.S_i;
+    I.S = d.S_d;
+    I.status = gs;
+    if (gs != CL_OK && first_bad == CL_OK) first_bad = gs;
+  }
+  if (first_bad != CL_OK) {
+    delete p;
+    return first_bad;
+  }
+  p->n_items = items;
+  p->psize = pbase;
+  p->ntiles = p->tile_begin[G];
+
+  // launch shape (performance knobs only)
+  p->block = (tuning && tuning->block > 0) ? tuning->block : 256;
+  if (p->block % 32 != 0 || p->block > 256) {
+    delete p;
+    return CL_ERR_INVALID_ARG;
+  }
+  int bps_c = sampler_max_blocks_per_sm(p->block, false, 0);
+  int bps_e32 = sampler_max_blocks_per_sm(p->block, true, CL_E_I32);
+  int bps_e64 = sampler_max_blocks_per_sm(p->block, true, CL_E_I64);
+  if (tuning && tuning->blocks_per_sm > 0) {
+    bps_c = bps_c < tuning->blocks_per_sm ? bps_c : tuning->blocks_per_sm;
+    bps_e32 = bps_e32 < tuning->blocks_per_sm ? bps_e32 : tuning->blocks_per_sm;
+    bps_e64 = bps_e64 < tuning->blocks_per_sm ? bps_e64 : tuning->blocks_per_sm;
+  }
+  p->grid_count = p->sms * (bps_c > 0 ? bps_c : 1);
+  p->grid_emit32 = p->sms * (bps_e32 > 0 ? bps_e32 : 1);
+  p->grid_emit64 = p->sms * (bps_e64 > 0 ? bps_e64 : 1);
+  long long warps = (long long)p->grid_count * (p->block / 32);
+  long long T = (tuning && tuning->tasks > 0) ? tuning->tasks : 16 * warps;
+  long long cap = (items + 31) / 32;
+  if (T > cap) T = cap;
+  if (T < 1) T = 1;
+  if (T > (1ll << 30)) T = 1ll << 30;
+  p->T = (int)T;
+  *out = p;
+  return CL_OK;
+}
+
+cl_status cl_plan_workspace_bytes(const cl_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return CL_ERR_INVALID_ARG;
+  *bytes = ws_layout(nullptr, plan).bytes;
+  return CL_OK;
+}
+
+cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t stream) {
+  if (!p) return CL_ERR_INVALID_ARG;
+  WsLayout L = ws_layout(d_ws, p);
+  if (!d_ws || ws_bytes < L.bytes) return CL_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  p->ws_bytes = ws_bytes;
+  p->d_graphs = L.graphs;
+  p->d_tile_begin = L.tile_begin;
+  p->d_P = L.P;
+  p->d_C = L.C;
+  p->d_part = L.part;
+  p->d_scan_part = L.scan_part;
+  p->d_task = L.task;
+  p->d_ctr = L.ctr;
+  p->d_err = L.err;
+  p->d_stats = L.stats;
+  cl_status st;
+  if ((st = cuda_ok(cudaMemcpyAsync(L.graphs, p->dg.data(), sizeof(DevGraph) * p->G, cudaMemcpyHostToDevice, s))))
+    return st;
+  if ((st = cuda_ok(cudaMemcpyAsync(L.tile_begin, p->tile_begin.data(), sizeof(long long) * (p->G + 1),
+                                    cudaMemcpyHostToDevice, s))))
+    return st;
+  if ((st = cuda_ok(cudaMemsetAsync(L.ctr, 0, 4 * sizeof(unsigned) + 0, s)))) return st;
+  if ((st = cuda_ok(cudaMemsetAsync(L.err, 0, 4 * sizeof(int), s)))) return st;
+  if ((st = cuda_ok(cudaMemsetAsync(L.stats, 0, 4 * sizeof(unsigned long long), s)))) return st;
+  launch_weight_prefix(L.graphs, L.tile_begin, p->G, p->ntiles, L.P, L.part, s);
+  launch_costs_and_tasks(L.graphs, p->G, p->n_items, L.P, L.C, L.part, L.task, p->T, s);
+  if ((st = last_ok())) return st;
+  p->built = true;
+  return CL_OK;
+}
+
+cl_status cl_plan_items(const cl_plan* plan, int64_t* n_items) {
+  if (!plan || !n_items) return CL_ERR_INVALID_ARG;
+  *n_items = plan->n_items;
+  return CL_OK;
+}
+
+cl_status cl_plan_graph_info(const cl_plan* plan, int32_t g, cl_graph_info* out) {
+  if (!plan || !out || g < 0 || g >= plan->G) return CL_ERR_INVALID_ARG;
+  *out = plan->info[g];
+  return CL_OK;
+}
+
+cl_status cl_count(cl_plan* p, int32_t* d_counts, cl_stream_t stream) {
+  if (!p || (!d_counts && p->n_items > 0)) return CL_ERR_INVALID_ARG;
+  if (!p->built) return CL_ERR_STATE;
+  if (p->n_items == 0) return CL_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s);
+  launch_count(dev_plan(p), d_counts, p->block, p->grid_count, s);
+  return last_ok();
+}
+
+cl_status cl_scan(cl_plan* p, const int32_t* d_counts, int64_t* d_offsets, int64_t* h_total, cl_stream_t stream) {
+  if (!p || !d_offsets || (!d_counts && p->n_items > 0)) return CL_ERR_INVALID_ARG;
+  if (!p->built) return CL_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_count_scan(d_counts, p->n_items, (long long*)d_offsets, p->d_scan_part, s);
+  cl_status st = last_ok();
+  if (st != CL_OK || !h_total) return st;
+  int err = 0;
+  if ((st = cuda_ok(cudaMemcpyAsync(h_total, d_offsets + p->n_items, sizeof(int64_t), cudaMemcpyDeviceToHost, s))))
+    return st;
+  if ((st = cuda_ok(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)))) return st;
+  if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
+  return err ? CL_ERR_DEVICE : CL_OK;
+}
+
+cl_status cl_emit(cl_plan* p, const int64_t* d_offsets, int32_t etype, void* d_edges, int64_t capacity,
+                  int64_t item_begin, int64_t item_end, cl_stream_t stream) {
+  if (!p || !d_offsets || capacity < 0) return CL_ERR_INVALID_ARG;
+  if (etype != CL_E_I32 && etype != CL_E_I64) return CL_ERR_INVALID_ARG;
+  if (item_begin < 0 || item_end < item_begin || item_end > p->n_items) return CL_ERR_INVALID_ARG;
+  if (capacity > 0 && !d_edges) return CL_ERR_INVALID_ARG;
+  if (!p->built) return CL_ERR_STATE;
+  if (item_end == item_begin) return CL_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_emit(dev_plan(p), (const long long*)d_offsets, item_begin, item_end, etype, d_edges, capacity, p->block,
+              etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, s);
+  return last_ok();
+}
+
+cl_status cl_generate_batch(cl_plan* p, int32_t etype, void* d_edges, int64_t capacity, int64_t* d_graph_offsets,
+                            int32_t* d_counts, int64_t* d_offsets, int32_t* d_status, cl_stream_t stream) {
+  if (!p || !d_graph_offsets || !d_offsets || !d_status || capacity < 0) return CL_ERR_INVALID_ARG;
+  if (etype != CL_E_I32 && etype != CL_E_I64) return CL_ERR_INVALID_ARG;
+  if (p->n_items > 0 && !d_counts) return CL_ERR_INVALID_ARG;
+  if (capacity > 0 && !d_edges) return CL_ERR_INVALID_ARG;
+  if (!p->built) return CL_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cl_status st;
+  if ((st = cl_count(p, d_counts, stream))) return st;
+  if ((st = cl_scan(p, d_counts, d_offsets, nullptr, stream))) return st;
+  launch_graph_offsets(p->d_graphs, p->G, (const long long*)d_offsets, p->n_items, (long long*)d_graph_offsets,
+                       capacity, d_status, s);
+  if ((st = last_ok())) return st;
+  if (p->n_items == 0) return CL_OK;
+  launch_emit(dev_plan(p), (const long long*)d_offsets, 0, p->n_items, etype, d_edges, capacity, p->block,
+              etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, s);
+  return last_ok();
+}
+
+cl_status cl_stats(cl_plan* p, cl_run_stats* out, cl_stream_t stream) {
+  if (!p || !out) return CL_ERR_INVALID_ARG;
+  if (!p->built) return CL_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long st[4] = {0, 0, 0, 0};
+  int err = 0;
+  cl_status r;
+  if ((r = cuda_ok(cudaMemcpyAsync(st, p->d_stats, sizeof(st), cudaMemcpyDeviceToHost, s)))) return r;
+  if ((r = cuda_ok(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)))) return r;
+  if ((r = cuda_ok(cudaStreamSynchronize(s)))) return r;
+  out->iterations = (int64_t)st[0];
+  out->fallbacks = (int64_t)st[1];
+  out->ties = (int64_t)st[2];
+  out->error = err;
+  cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
+  return cuda_ok(cudaStreamSynchronize(s));
+}
+
+cl_status cl_check(cl_plan* p, cl_stream_t stream) {
+  if (!p) return CL_ERR_INVALID_ARG;
+  if (!p->built) return CL_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  int err = 0;
+  cl_status r;
+  if ((r = cuda_ok(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)))) return r;
+  if ((r = cuda_ok(cudaStreamSynchronize(s)))) return r;
+  cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
+  if ((r = cuda_ok(cudaStreamSynchronize(s)))) return r;
+  return (cl_status)err;
+}
+
+void cl_plan_destroy(cl_plan* p) { delete p; }
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// cl_internal.cuh -- device-side plan layout shared by the library's kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/cl.h"
+
+namespace cl {
+
+constexpr int SEG_LOG2 = 16;  // heavy rows are cut at absolute multiples of 2^16 of v
+constexpr unsigned LIGHT_SEG = 0xFFFFFFFFu;
+constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
+
+// One graph of a plan, as the kernels see it (lives in the plan workspace).
+struct DevGraph {
+  const void* w;          // device weights, sorted non-increasing
+  long long n;            // nodes
+  long long S_i;          // exact integer sum (integer weights)
+  double S_d;             // weight sum as a double
+  unsigned key0, key1;    // Philox key = seed
+  long long H;            // heavy rows (w_u >= heavy_w): a prefix
+  long long Hh;           // heavy rows that have items: min(H, n - 1)
+  long long n_heavy;      // items of the heavy rows
+  long long item_begin;   // first global item
+  long long n_items;      // items of this graph
+  long long pbase;        // offset of this graph's weight prefix (n + 1 entries)
+  int wtype;              // cl_wtype
+  int pad_;
+};
+
+// Per-graph results of the analysis kernel (scratch of cl_plan_create).
+struct GraphAnalysis {
+  unsigned long long S_i;       // integer sum
+  unsigned long long H;         // count of w >= heavy_w
+  unsigned int flags;           // bit 0: unsorted, bit 1: negative / non-finite
+  unsigned int pad_;
+  double S_d;                   // correctly rounded sum (double weights)
+};
+
+// Items of heavy rows [0, U): sum_{u<U} K_u, K_u = N1 - ((u+1) >> 16) + 1,
+// N1 = (n-1) >> 16; uses sum_{x=0}^{U} floor(x / 2^16) in closed form.
+__host__ __device__ __forceinline__ long long heavy_items_before(long long U, long long n) {
+  const long long B = 1ll << SEG_LOG2;
+  long long N1 = (n - 1) >> SEG_LOG2;
+  long long q = U >> SEG_LOG2;
+  long long F = B * q * (q - 1) / 2 + q * (U - q * B + 1);
+  return U * (N1 + 1) - F;
+}
+
+// Bounds of a graph's local item: source row u, segment field, [j0, end).
+__device__ __forceinline__ void item_bounds(const DevGraph& g, long long local, unsigned& u, unsigned& seg,
+                                            unsigned& j0, unsigned& end) {
+  if (local >= g.n_heavy) {
+    u = (unsigned)(g.H + (local - g.n_heavy));
+    seg = LIGHT_SEG;
+    j0 = u + 1;
+    end = (unsigned)g.n;
+    return;
+  }
+  long long lo = 0, hi = g.Hh - 1;  // last r with heavy_items_before(r) <= local
+  while (lo < hi) {
+    long long mid = (lo + hi + 1) >> 1;
+    if (heavy_items_before(mid, g.n) <= local)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  long long k = ((lo + 1) >> SEG_LOG2) + (local - heavy_items_before(lo, g.n));
+  long long s0 = k << SEG_LOG2, s1 = (k + 1) << SEG_LOG2;
+  u = (unsigned)lo;
+  seg = (unsigned)k;
+  j0 = (unsigned)(s0 > lo + 1 ? s0 : lo + 1);
+  end = (unsigned)(s1 < g.n ? s1 : g.n);
+}
+
+// Graph owning a global item (binary search over item_begin; G is small).
+__device__ __forceinline__ int graph_of_item(const DevGraph* gs, int G, long long item) {
+  int lo = 0, hi = G - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (gs[mid].item_begin <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Kernel-facing view of a built plan.
+struct DevPlan {
+  const DevGraph* graphs;
+  int G;
+  long long n_items;
+  const long long* task_start;  // T + 1 entries
+  int T;
+  unsigned* task_ctr;           // dynamic task counter (reset before each sampler launch)
+  int* err;                     // device error word (first error wins)
+  unsigned long long* stats;    // iterations, fallbacks, ties
+};
+
+// ---- launchers implemented in plan.cu / sample.cu / diag.cu ----
+constexpr int ANALYZE_CHUNK_HOST = 4096;  // weights per analysis block (matches plan.cu)
+constexpr int SCAN_TILE_HOST = 2048;      // elements per scan tile (matches plan.cu)
+void launch_analyze(const DevGraph* d_graphs, const long long* d_blk_begin, int G, long long nblocks,
+                    const double* d_heavy_w, GraphAnalysis* d_out, unsigned long long* d_bins, bool f64,
+                    cudaStream_t s);
+void launch_f64_sum_finalize(int G, const unsigned long long* d_bins, GraphAnalysis* d_out, cudaStream_t s);
+size_t f64_bins_bytes(int G);
+
+// Weight prefix P_g[u] = sum_{v<u} w_v for u = 0..n_g (as double), tile-segmented by graph.
+void launch_weight_prefix(const DevGraph* d_graphs, const long long* d_tile_graph_begin, int G, long long ntiles,
+                          double* d_P, double* d_partials, cudaStream_t s);
+// Item costs c_i, inclusive prefix C in place, task boundaries (Eq. 3).
+void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, const double* d_P, double* d_C,
+                            double* d_partials, long long* d_task_start, int T, cudaStream_t s);
+// Exclusive int32 -> int64 scan with the total at out[n].
+void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, long long* d_partials,
+                       cudaStream_t s);
+long long scan_partials_needed(long long n);
+
+void launch_count(const DevPlan& P, int* d_counts, int block, int grid, cudaStream_t s);
+void launch_emit(const DevPlan& P, const long long* d_offsets, long long ib, long long ie, int etype, void* d_edges,
+                 long long capacity, int block, int grid, cudaStream_t s);
+void launch_graph_offsets(const DevGraph* d_graphs, int G, const long long* d_offsets, long long n_items,
+                          long long* d_graph_offsets, long long capacity, int* d_status, cudaStream_t s);
+int sampler_max_blocks_per_sm(int block, bool emit, int etype);
+
+}  // namespace cl

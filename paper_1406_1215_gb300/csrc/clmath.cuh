@@ -1,0 +1,276 @@
+// clmath.cuh -- device arithmetic for the exact skip length of Algorithm 1.
+//
+// The skip of Algorithm 1 is delta = floor(ln r / ln(1 - p)).  This library
+// defines delta as the floor of that exact real number (r = (2k+1)/2^53,
+// p = Q/S with integers Q < S), and evaluates it in two tiers:
+//
+//   1. float-float (pairs of FP32, ~46 bits): x = L_r / L_p with
+//      L_r = -ln(r), L_p = -ln(1 - p); accepted when x is farther than
+//      2^-40 x from an integer.  FP64 runs at 1/75 of FP32 on this GPU, so the
+//      per-candidate path uses only FP32 and integer pipes.
+//   2. double-double (~104 bits) when tier 1 cannot decide; accepted when x is
+//      farther than 2^-96 x from an integer; otherwise the nearest integer is
+//      taken (which is right when x is exactly an integer) and counted.
+//
+// Both logarithms are of a ratio of integers, -ln(A/B) with 1 <= A < B,
+// computed by table-driven argument reduction (Tang, ACM TOMS 15(2), 1989/90)
+// and the atanh series:
+//   A' = A 2^e in [B/2, B);  J = round(64 A'/B) in [32, 64];
+//   -ln(A/B) = e ln2 + ln(64/J) - 2 atanh(s),  s = (64A' - JB) / (64A' + JB),
+// where s is formed from exact integers, so no cancellation is lost for
+// p -> 0 (A -> B) or p -> 1 (A -> 0).  |s| <= ~1/127.
+//
+// Float-float and double-double arithmetic follow Dekker (1971) and Knuth
+// (TAOCP vol. 2, 4.2.2): error-free TwoSum, TwoProd via fused multiply-add.
+#pragma once
+#include <cstdint>
+
+#include "ln_tables.h"
+
+namespace cl {
+
+// ----------------------------------------------------------------- float-float
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+  ff s = ff_two_sum(x.hi, y.hi);
+  ff t = ff_two_sum(x.lo, y.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = ff_fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  ff p = ff_two_prod(x.hi, y.hi);
+  p.lo = fmaf(x.hi, y.lo, p.lo);
+  p.lo = fmaf(x.lo, y.hi, p.lo);
+  return ff_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_mul_f(ff x, float y) {
+  ff p = ff_two_prod(x.hi, y);
+  p.lo = fmaf(x.lo, y, p.lo);
+  return ff_fast_two_sum(p.hi, p.lo);
+}
+// x / y: first quotient from the rounded reciprocal, one correction from the
+// residual x - q1 y (q1 * y.hi is exact as a TwoProd; x.hi - p.hi is exact by
+// Sterbenz' lemma since q1 y.hi is within a few ulps of x.hi).
+__device__ __forceinline__ ff ff_div(ff x, ff y) {
+  float r = __frcp_rn(y.hi);
+  float q1 = __fmul_rn(x.hi, r);
+  ff p = ff_two_prod(q1, y.hi);
+  float e = __fsub_rn(x.hi, p.hi);
+  e = __fsub_rn(e, p.lo);
+  e = __fadd_rn(e, x.lo);
+  e = fmaf(-q1, y.lo, e);
+  float q2 = __fmul_rn(e, r);
+  return ff_fast_two_sum(q1, q2);
+}
+// signed 64-bit integer (|v| < 2^62) to float-float, ~48 significant bits
+__device__ __forceinline__ ff ff_from_i64(long long v) {
+  float hi = __ll2float_rn(v);
+  float lo = __ll2float_rn(v - __float2ll_rz(hi));
+  return {hi, lo};
+}
+
+// -ln(A / B) for integers 1 <= A < B <= 2^55, as float-float.
+__device__ __forceinline__ ff ff_neglog_ratio(unsigned long long A, unsigned long long B) {
+  int e = __clzll(A) - __clzll(B);
+  unsigned long long Ap = A << e;
+  if (Ap >= B) {
+    Ap >>= 1;
+    e -= 1;
+  }
+  // J = round(64 A'/B) from the top 24 bits (an off-by-one J only widens |s| slightly)
+  int sh = 40 - __clzll(B);
+  sh = sh < 0 ? 0 : sh;
+  float fa = __uint2float_rn((unsigned)(Ap >> sh));
+  float fb = __uint2float_rn((unsigned)(B >> sh));
+  int J = __float2int_rn(__fdividef(64.0f * fa, fb));
+  J = J < 32 ? 32 : (J > 64 ? 64 : J);
+  long long N = (long long)(Ap << 6) - (long long)J * (long long)B;
+  long long D = (long long)(Ap << 6) + (long long)J * (long long)B;
+  ff s = ff_div(ff_from_i64(N), ff_from_i64(D));
+  // atanh(s) = s (1 + z (1/3 + z/5 + z^2/7 + z^3/9)), z = s^2
+  ff z = ff_two_prod(s.hi, s.hi);
+  z.lo = fmaf(2.0f * s.hi, s.lo, z.lo);
+  z = ff_fast_two_sum(z.hi, z.lo);
+  float tail = z.hi * fmaf(z.hi, fmaf(z.hi, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f);
+  ff P2 = ff_add(ff{CL_THIRD_FF_HI, CL_THIRD_FF_LO}, ff{tail, 0.0f});
+  ff c = ff_mul(z, P2);   // z (1/3 + ...)
+  ff sc = ff_mul(s, c);   // s z (...)
+  ff at = ff_add(s, sc);  // atanh(s)
+  ff t = ff{__ldg(&CL_LNT_FF[J - 32][0]), __ldg(&CL_LNT_FF[J - 32][1])};
+  ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, (float)e);
+  ff r = ff_add(le, t);
+  return ff_add(r, ff{-2.0f * at.hi, -2.0f * at.lo});
+}
+
+// ------------------------------------------------------------- double-double
+struct dd {
+  double hi, lo;
+};
+
+__device__ __forceinline__ dd dd_two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dd dd_fast_two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ __forceinline__ dd dd_two_prod(double a, double b) {
+  double p = __dmul_rn(a, b);
+  return {p, fma(a, b, -p)};
+}
+__device__ __forceinline__ dd dd_add(dd x, dd y) {
+  dd s = dd_two_sum(x.hi, y.hi);
+  dd t = dd_two_sum(x.lo, y.lo);
+  s.lo = __dadd_rn(s.lo, t.hi);
+  s = dd_fast_two_sum(s.hi, s.lo);
+  s.lo = __dadd_rn(s.lo, t.lo);
+  return dd_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dd dd_mul(dd x, dd y) {
+  dd p = dd_two_prod(x.hi, y.hi);
+  p.lo = fma(x.hi, y.lo, p.lo);
+  p.lo = fma(x.lo, y.hi, p.lo);
+  return dd_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ dd dd_mul_d(dd x, double y) {
+  dd p = dd_two_prod(x.hi, y);
+  p.lo = fma(x.lo, y, p.lo);
+  return dd_fast_two_sum(p.hi, p.lo);
+}
+// x / y with three quotient digits (each from the exact residual)
+__device__ __forceinline__ dd dd_div(dd x, dd y) {
+  double q1 = __ddiv_rn(x.hi, y.hi);
+  dd r = dd_add(x, dd_mul_d(y, -q1));
+  double q2 = __ddiv_rn(r.hi, y.hi);
+  r = dd_add(r, dd_mul_d(y, -q2));
+  double q3 = __ddiv_rn(r.hi, y.hi);
+  dd q = dd_fast_two_sum(q1, q2);
+  return dd_add(q, dd{q3, 0.0});
+}
+__device__ __forceinline__ dd dd_from_i64(long long v) {
+  double hi = __ll2double_rn(v);
+  return {hi, __ll2double_rn(v - __double2ll_rz(hi))};
+}
+
+// -ln(A / B) for integers 1 <= A < B <= 2^55, as double-double.
+__device__ __forceinline__ dd dd_neglog_ratio(unsigned long long A, unsigned long long B) {
+  int e = __clzll(A) - __clzll(B);
+  unsigned long long Ap = A << e;
+  if (Ap >= B) {
+    Ap >>= 1;
+    e -= 1;
+  }
+  int J = __double2int_rn(64.0 * __ull2double_rn(Ap) / __ull2double_rn(B));
+  J = J < 32 ? 32 : (J > 64 ? 64 : J);
+  long long N = (long long)(Ap << 6) - (long long)J * (long long)B;
+  long long D = (long long)(Ap << 6) + (long long)J * (long long)B;
+  dd s = dd_div(dd_from_i64(N), dd_from_i64(D));
+  dd z = dd_mul(s, s);
+  // sum_{k=0}^{9} z^k / (2k+1), Horner from the top
+  dd p = dd{__ldg(&CL_ATANH_DD[9][0]), __ldg(&CL_ATANH_DD[9][1])};
+  for (int k = 8; k >= 0; --k) p = dd_add(dd_mul(p, z), dd{__ldg(&CL_ATANH_DD[k][0]), __ldg(&CL_ATANH_DD[k][1])});
+  dd at = dd_mul(s, p);
+  dd t = dd{__ldg(&CL_LNT_DD[J - 32][0]), __ldg(&CL_LNT_DD[J - 32][1])};
+  dd le = dd_mul_d(dd{CL_LN2_DD_HI, CL_LN2_DD_LO}, (double)e);
+  dd r = dd_add(le, t);
+  return dd_add(r, dd{-2.0 * at.hi, -2.0 * at.lo});
+}
+
+// ------------------------------------------------------------ skip decision
+// Outcome of one tier: the floor of x clamped at R, or "undecided".
+static constexpr long long SKIP_UNDECIDED = -1;
+
+// x = hi + lo >= 0: floor(x) clamped at R, when x is farther than
+// margin = tau * x from every integer (tau = 2^-40 for float-float).
+// x - k0 (k0 = floor(hi)) is formed exactly; the distances of x to floor(x)
+// and floor(x) + 1 are then each computed with one rounding, so a decision
+// is safe whenever the evaluation error of x is below margin / 2.
+__device__ __forceinline__ long long floor_decide_ff(ff x, long long R) {
+  const float tau = 0x1p-40f;
+  if (x.hi > 0x1p33f || x.hi > (float)R * (1.0f + 0x1p-20f)) return R;  // x >= R for sure
+  float k0 = floorf(x.hi);
+  ff r = ff_two_sum(__fsub_rn(x.hi, k0), x.lo);  // x - k0, exact, in (-1/2, 1)
+  long long k;
+  float dlo, dhi;  // distances from x to k and to k + 1
+  if (r.hi < 0.0f) {  // x just below k0 (x.hi integral, x.lo < 0)
+    k = (long long)k0 - 1;
+    dhi = __fsub_rn(-r.hi, r.lo);
+    dlo = __fadd_rn(1.0f, r.hi);
+  } else if (r.hi > 1.0f || (r.hi == 1.0f && r.lo >= 0.0f)) {
+    k = (long long)k0 + 1;
+    dlo = __fadd_rn(__fsub_rn(r.hi, 1.0f), r.lo);
+    dhi = __fsub_rn(1.0f, dlo);
+  } else {
+    k = (long long)k0;
+    dlo = __fadd_rn(r.hi, r.lo);
+    dhi = __fsub_rn(__fsub_rn(1.0f, r.hi), r.lo);
+  }
+  float margin = tau * x.hi;
+  if (!(dlo > margin) || !(dhi > margin)) return SKIP_UNDECIDED;
+  return k < R ? k : R;
+}
+
+// Same for double-double with tau = 2^-96; an undecided x takes the nearest
+// integer (*tie = true), which is the exact floor when x is an integer.
+__device__ __forceinline__ long long floor_decide_dd(dd x, long long R, bool* tie) {
+  const double tau = 0x1p-96;
+  *tie = false;
+  if (x.hi > 0x1p40 || x.hi > (double)R * (1.0 + 0x1p-40)) return R;
+  double k0 = floor(x.hi);
+  dd r = dd_two_sum(__dsub_rn(x.hi, k0), x.lo);
+  long long k;
+  double dlo, dhi;
+  if (r.hi < 0.0) {
+    k = (long long)k0 - 1;
+    dhi = __dsub_rn(-r.hi, r.lo);
+    dlo = __dadd_rn(1.0, r.hi);
+  } else if (r.hi > 1.0 || (r.hi == 1.0 && r.lo >= 0.0)) {
+    k = (long long)k0 + 1;
+    dlo = __dadd_rn(__dsub_rn(r.hi, 1.0), r.lo);
+    dhi = __dsub_rn(1.0, dlo);
+  } else {
+    k = (long long)k0;
+    dlo = __dadd_rn(r.hi, r.lo);
+    dhi = __dsub_rn(__dsub_rn(1.0, r.hi), r.lo);
+  }
+  double margin = tau * x.hi;
+  if (!(dlo > margin) || !(dhi > margin)) {
+    *tie = true;
+    if (dhi < dlo) k += 1;  // nearest integer
+  }
+  return k < R ? k : R;
+}
+
+// Tier-2 skip: x = -ln(Ar / 2^53) / -ln(Ap / S) in double-double.
+static __device__ __noinline__ long long skip_fallback_dd(unsigned long long Ar, unsigned long long Ap,
+                                                   unsigned long long S, long long R, bool* tie) {
+  dd Lr = dd_neglog_ratio(Ar, 1ull << 53);
+  dd Lp = dd_neglog_ratio(Ap, S);
+  return floor_decide_dd(dd_div(Lr, Lp), R, tie);
+}
+
+}  // namespace cl

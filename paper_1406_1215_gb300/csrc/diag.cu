@@ -1,0 +1,121 @@
+// diag.cu -- diagnostic entry points: each applies one device primitive of the
+// sampler to arrays, so that tests can compare it element by element with an
+// independent implementation (cuRAND's Philox, the CPU oracle's skip).
+#include <cuda_runtime.h>
+#include <curand_kernel.h>
+
+#include "cl_internal.cuh"
+#include "clmath.cuh"
+#include "philox.cuh"
+
+namespace cl {
+
+__global__ void diag_philox_kernel(const uint32_t* __restrict__ ctr, long long n, uint32_t k0, uint32_t k1,
+                                   uint32_t* __restrict__ out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u32x4 c{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+  u32x4 r = philox4x32_10(c, k0, k1);
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+// cuRAND's device Philox4x32-10, called (not copied) as an independent reference.
+__global__ void diag_philox_curand_kernel(const uint32_t* __restrict__ ctr, long long n, uint32_t k0, uint32_t k1,
+                                          uint32_t* __restrict__ out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  uint4 r = curand_Philox4x32_10(c, make_uint2(k0, k1));
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+__global__ void diag_neglog_kernel(const unsigned long long* __restrict__ A, const unsigned long long* __restrict__ B,
+                                   long long n, float* __restrict__ oft, double* __restrict__ odd) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!(A[i] >= 1 && A[i] < B[i] && B[i] <= (1ull << 55))) {  // outside the routine's domain
+    oft[2 * i] = oft[2 * i + 1] = __int_as_float(0x7fc00000);
+    odd[2 * i] = odd[2 * i + 1] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  ff f = ff_neglog_ratio(A[i], B[i]);
+  dd d = dd_neglog_ratio(A[i], B[i]);
+  oft[2 * i] = f.hi;
+  oft[2 * i + 1] = f.lo;
+  odd[2 * i] = d.hi;
+  odd[2 * i + 1] = d.lo;
+}
+
+// The same two-tier decision the sampler makes for one skip.
+__global__ void diag_skip_kernel(const unsigned long long* __restrict__ a, const unsigned long long* __restrict__ Q,
+                                 const unsigned long long* __restrict__ S, const long long* __restrict__ R,
+                                 long long n, long long* __restrict__ delta, int* __restrict__ tier) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!(Q[i] > 0 && Q[i] < S[i] && S[i] < (1ull << 53) && a[i] < (1ull << 52) && R[i] >= 1)) {
+    delta[i] = -2;  // outside the domain of the skip
+    tier[i] = -1;
+    return;
+  }
+  unsigned long long Ar = 2ull * a[i] + 1ull;
+  ff Lr = ff_neglog_ratio(Ar, 1ull << 53);
+  ff Lp = ff_neglog_ratio(S[i] - Q[i], S[i]);
+  long long d = floor_decide_ff(ff_div(Lr, Lp), R[i]);
+  int tr = 0;
+  if (d == SKIP_UNDECIDED) {
+    bool tie;
+    d = skip_fallback_dd(Ar, S[i] - Q[i], S[i], R[i], &tie);
+    tr = tie ? 2 : 1;
+  }
+  delta[i] = d;
+  tier[i] = tr;
+}
+
+}  // namespace cl
+
+using namespace cl;
+
+static cl_status diag_done() { return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA; }
+
+extern "C" cl_status cl_diag_philox(const uint32_t* d_ctr, int64_t count, uint64_t seed, uint32_t* d_out,
+                                    cl_stream_t stream) {
+  if (count < 0 || (count > 0 && (!d_ctr || !d_out))) return CL_ERR_INVALID_ARG;
+  if (count == 0) return CL_OK;
+  diag_philox_kernel<<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      d_ctr, count, (uint32_t)seed, (uint32_t)(seed >> 32), d_out);
+  return diag_done();
+}
+
+extern "C" cl_status cl_diag_philox_curand(const uint32_t* d_ctr, int64_t count, uint64_t seed, uint32_t* d_out,
+                                           cl_stream_t stream) {
+  if (count < 0 || (count > 0 && (!d_ctr || !d_out))) return CL_ERR_INVALID_ARG;
+  if (count == 0) return CL_OK;
+  diag_philox_curand_kernel<<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      d_ctr, count, (uint32_t)seed, (uint32_t)(seed >> 32), d_out);
+  return diag_done();
+}
+
+extern "C" cl_status cl_diag_neglog(const uint64_t* d_A, const uint64_t* d_B, int64_t count, float* d_ff, double* d_dd,
+                                    cl_stream_t stream) {
+  if (count < 0 || (count > 0 && (!d_A || !d_B || !d_ff || !d_dd))) return CL_ERR_INVALID_ARG;
+  if (count == 0) return CL_OK;
+  diag_neglog_kernel<<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      (const unsigned long long*)d_A, (const unsigned long long*)d_B, count, d_ff, d_dd);
+  return diag_done();
+}
+
+extern "C" cl_status cl_diag_skip(const uint64_t* d_a, const uint64_t* d_Q, const uint64_t* d_S, const int64_t* d_R,
+                                  int64_t count, int64_t* d_delta, int32_t* d_tier, cl_stream_t stream) {
+  if (count < 0 || (count > 0 && (!d_a || !d_Q || !d_S || !d_R || !d_delta || !d_tier))) return CL_ERR_INVALID_ARG;
+  if (count == 0) return CL_OK;
+  diag_skip_kernel<<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      (const unsigned long long*)d_a, (const unsigned long long*)d_Q, (const unsigned long long*)d_S,
+      (const long long*)d_R, count, (long long*)d_delta, d_tier);
+  return diag_done();
+}

@@ -1,0 +1,483 @@
+// plan.cu -- planning kernels: validation and the exact sum S (Algorithm 1,
+// first line; Section 4's parallel sum), the weight prefix sigma, item costs
+// (Eq. 1-2, Eq. 6), their inclusive prefix (Calc-Cost of Algorithm 2 as a
+// device-wide scan) and the task boundaries of Eq. 3.  Also the int32 ->
+// int64 exclusive scan that turns per-item edge counts into offsets.
+//
+// Scans are three-phase (tile reduce, scan of tile partials, tile scan): no
+// block ever waits on another block.
+#include <cuda_runtime.h>
+
+#include "cl_internal.cuh"
+
+namespace cl {
+
+constexpr int PLAN_THREADS = 256;
+constexpr int ANALYZE_CHUNK = 4096;  // weights per analysis block
+constexpr int SCAN_ITEMS = 8;        // items per thread in a scan tile
+constexpr int SCAN_TILE = PLAN_THREADS * SCAN_ITEMS;
+constexpr int F64_BINS = 2048;       // one bin per biased double exponent
+
+// --------------------------------------------------------------- block scans
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T x = __shfl_up_sync(FULL_MASK, v, o);
+    if (lane >= o) v += x;
+  }
+  return v;
+}
+
+// Exclusive block scan of one value per thread; returns the block total in *total.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* total) {
+  __shared__ T warp_tot[32];
+  __shared__ T block_tot;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T t = lane < nw ? warp_tot[lane] : T(0);
+    T ti = warp_incl_scan(t);
+    if (lane < nw) warp_tot[lane] = ti - t;
+    if (lane == nw - 1) block_tot = ti;
+  }
+  __syncthreads();
+  T res = warp_tot[wid] + inc - v;
+  *total = block_tot;
+  __syncthreads();
+  return res;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_reduce(T v) {
+  __shared__ T red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T t = T(0);
+  if (wid == 0) {
+    t = lane < nw ? red[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL_MASK, t, o);
+  }
+  __syncthreads();
+  return t;  // valid in warp 0
+}
+
+// Single-block exclusive scan of n partials in place; optional segment heads
+// (head[i] != 0 restarts the running sum at i).  Returns nothing; total unused.
+template <typename T>
+__global__ void partials_scan_kernel(T* __restrict__ part, long long n, const unsigned char* __restrict__ head) {
+  __shared__ T carry_s;
+  if (threadIdx.x == 0) carry_s = T(0);
+  __syncthreads();
+  for (long long base = 0; base < n; base += blockDim.x) {
+    long long i = base + threadIdx.x;
+    T v = i < n ? part[i] : T(0);
+    bool h = (head != nullptr && i < n) ? head[i] != 0 : false;
+    T carry = carry_s;
+    if (head == nullptr) {
+      T tot;
+      T ex = block_excl_scan(v, &tot);
+      if (i < n) part[i] = carry + ex;
+      if (threadIdx.x == 0) carry_s = carry + tot;
+      __syncthreads();
+    } else {
+      // segmented: sequential within the chunk by thread 0 (partials are few)
+      __shared__ T vals[1024];
+      __shared__ unsigned char hs[1024];
+      vals[threadIdx.x] = v;
+      hs[threadIdx.x] = h;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        T run = carry;
+        long long lim = n - base < (long long)blockDim.x ? n - base : (long long)blockDim.x;
+        for (long long k = 0; k < lim; ++k) {
+          if (hs[k]) run = T(0);
+          T x = vals[k];
+          vals[k] = run;
+          run += x;
+        }
+        carry_s = run;
+      }
+      __syncthreads();
+      if (i < n) part[i] = vals[threadIdx.x];
+      __syncthreads();
+    }
+  }
+}
+
+// --------------------------------------------------------------- analysis
+__device__ __forceinline__ int block_graph(const long long* blk_begin, int G, long long b) {
+  int lo = 0, hi = G - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (blk_begin[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// 128-bit bin add: lo with carry into hi (both 64-bit words, order independent).
+__device__ __forceinline__ void bin_add_shared(unsigned long long* lo, unsigned long long* hi, unsigned long long m) {
+  unsigned long long old = atomicAdd(lo, m);
+  if (old + m < old) atomicAdd(hi, 1ull);
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(PLAN_THREADS) analyze_kernel(const DevGraph* __restrict__ gs,
+                                                               const long long* __restrict__ blk_begin, int G,
+                                                               const double* __restrict__ heavy_w,
+                                                               GraphAnalysis* __restrict__ out,
+                                                               unsigned long long* __restrict__ bins) {
+  extern __shared__ unsigned long long sbins[];  // F64: 2 * F64_BINS words (lo, hi)
+  const long long b = blockIdx.x;
+  const int g = block_graph(blk_begin, G, b);
+  const DevGraph& gr = gs[g];
+  const long long lb = b - blk_begin[g];
+  const long long n = gr.n;
+  const double hw = heavy_w[g];
+  long long i0 = lb * ANALYZE_CHUNK;
+  long long i1 = i0 + ANALYZE_CHUNK < n ? i0 + ANALYZE_CHUNK : n;
+  unsigned flags = 0;
+  unsigned long long heavy = 0, sum = 0;
+  if (F64) {
+    for (int k = threadIdx.x; k < 2 * F64_BINS; k += blockDim.x) sbins[k] = 0;
+    __syncthreads();
+    const double* w = (const double*)gr.w;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      double x = w[i];
+      if (!(x >= 0.0) || !isfinite(x)) {
+        flags |= 2u;
+        continue;
+      }
+      if (i + 1 < n && x < w[i + 1]) flags |= 1u;
+      if (x >= hw) ++heavy;
+      unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+      int e = (int)(bits >> 52);
+      unsigned long long m = bits & ((1ull << 52) - 1);
+      if (e > 0) m |= 1ull << 52;
+      int bin = e > 0 ? e : 1;  // subnormals share the scale of the smallest normal
+      if (m) bin_add_shared(&sbins[2 * bin], &sbins[2 * bin + 1], m);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < F64_BINS; k += blockDim.x) {
+      unsigned long long lo = sbins[2 * k], hi = sbins[2 * k + 1];
+      unsigned long long* gb = bins + ((size_t)g * F64_BINS + k) * 2;
+      if (lo) bin_add_shared(&gb[0], &gb[1], lo);  // global atomics, same carry rule
+      if (hi) atomicAdd(&gb[1], hi);
+    }
+  } else {
+    const int* w = (const int*)gr.w;
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      int x = w[i];
+      if (x < 0) flags |= 2u;
+      if (i + 1 < n && x < w[i + 1]) flags |= 1u;
+      if ((double)x >= hw) ++heavy;
+      sum += (unsigned long long)(long long)x;
+    }
+  }
+  // block reductions
+  unsigned long long s = block_reduce(sum);
+  unsigned long long h = block_reduce(heavy);
+  unsigned f1 = __syncthreads_or(flags & 1u) ? 1u : 0u;
+  unsigned f2 = __syncthreads_or(flags & 2u) ? 2u : 0u;
+  unsigned f = f1 | f2;
+  if (threadIdx.x == 0) {
+    if (!F64 && s) atomicAdd(&out[g].S_i, s);
+    if (h) atomicAdd(&out[g].H, h);
+    if (f) atomicOr(&out[g].flags, f);
+  }
+}
+
+size_t f64_bins_bytes(int G) { return (size_t)G * F64_BINS * 2 * sizeof(unsigned long long); }
+
+// callers zero d_out (and, for double weights, the bins) beforehand
+void launch_analyze(const DevGraph* d_graphs, const long long* d_blk_begin, int G, long long nblocks,
+                    const double* d_heavy_w, GraphAnalysis* d_out, unsigned long long* d_bins, bool f64,
+                    cudaStream_t s) {
+  if (nblocks <= 0) return;
+  if (f64) {
+    size_t smem = 2 * F64_BINS * sizeof(unsigned long long);
+    cudaFuncSetAttribute(analyze_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    analyze_kernel<true><<<(unsigned)nblocks, PLAN_THREADS, smem, s>>>(d_graphs, d_blk_begin, G, d_heavy_w, d_out,
+                                                                       d_bins);
+  } else {
+    analyze_kernel<false><<<(unsigned)nblocks, PLAN_THREADS, 0, s>>>(d_graphs, d_blk_begin, G, d_heavy_w, d_out,
+                                                                     d_bins);
+  }
+}
+
+// Exact sum of double weights: the bins hold sum_b m_b 2^(b-1075) exactly as
+// 128-bit integers; one thread per graph forms the big integer (base 2^32
+// digits, bit 0 = 2^-1074) and rounds it once to nearest-even.
+__global__ void f64_sum_finalize_kernel(int G, const unsigned long long* __restrict__ bins,
+                                        GraphAnalysis* __restrict__ out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  constexpr int ND = 72;  // 2304 bits
+  unsigned long long acc[ND];
+  for (int d = 0; d < ND; ++d) acc[d] = 0;
+  const unsigned long long* gb = bins + (size_t)g * F64_BINS * 2;
+  for (int b = 1; b < F64_BINS - 1; ++b) {
+    unsigned long long lo = gb[2 * b], hi = gb[2 * b + 1];
+    if (!lo && !hi) continue;
+    int pos = b - 1;  // bit position of 2^(b-1075) relative to 2^-1074
+    // add lo at pos, hi at pos + 64, as 32-bit pieces
+    unsigned long long parts[4] = {lo & 0xFFFFFFFFull, lo >> 32, hi & 0xFFFFFFFFull, hi >> 32};
+    for (int k = 0; k < 4; ++k) {
+      if (!parts[k]) continue;
+      int p = pos + 32 * k;
+      int d = p >> 5, o = p & 31;
+      unsigned long long v = parts[k] << o;  // < 2^63
+      acc[d] += v & 0xFFFFFFFFull;
+      acc[d + 1] += v >> 32;
+    }
+  }
+  for (int d = 0; d + 1 < ND; ++d) {
+    acc[d + 1] += acc[d] >> 32;
+    acc[d] &= 0xFFFFFFFFull;
+  }
+  int top = -1;
+  for (int d = ND - 1; d >= 0 && top < 0; --d)
+    if (acc[d]) top = 32 * d + 31 - __clzll(acc[d] << 32);
+  double S = 0.0;
+  if (top >= 0) {
+    auto bit = [&](int p) -> unsigned long long {
+      return p < 0 ? 0ull : (acc[p >> 5] >> (p & 31)) & 1ull;
+    };
+    if (top <= 52) {
+      unsigned long long M = 0;
+      for (int p = top; p >= 0; --p) M = (M << 1) | bit(p);
+      S = __ll2double_rn((long long)M) * 0x1p-1074;  // exact (fits 53 bits)
+    } else {
+      unsigned long long M = 0;
+      for (int p = top; p > top - 53; --p) M = (M << 1) | bit(p);
+      int rb = top - 53;
+      unsigned long long round = bit(rb);
+      bool sticky = false;
+      for (int p = rb - 1; p >= 0 && !sticky; --p) sticky = bit(p) != 0;
+      if (round && (sticky || (M & 1ull))) ++M;
+      int ex = top - 52 - 1074;
+      if (M == (1ull << 53)) {
+        M >>= 1;
+        ++ex;
+      }
+      S = ldexp((double)M, ex);  // M has <= 53 bits: exact scaling unless it overflows
+    }
+  }
+  out[g].S_d = S;
+}
+
+void launch_f64_sum_finalize(int G, const unsigned long long* d_bins, GraphAnalysis* d_out, cudaStream_t s) {
+  f64_sum_finalize_kernel<<<(G + 31) / 32, 32, 0, s>>>(G, d_bins, d_out);
+}
+
+// --------------------------------------------------------------- weight prefix
+__device__ __forceinline__ double weight_at(const DevGraph& g, long long u) {
+  if (u >= g.n) return 0.0;
+  if (g.wtype == CL_W_F64) return ((const double*)g.w)[u];
+  return (double)((const int*)g.w)[u];
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS) wprefix_reduce_kernel(const DevGraph* __restrict__ gs,
+                                                                      const long long* __restrict__ tbeg, int G,
+                                                                      double* __restrict__ part,
+                                                                      unsigned char* __restrict__ head) {
+  const long long t = blockIdx.x;
+  const int g = block_graph(tbeg, G, t);
+  const DevGraph& gr = gs[g];
+  const long long lt = t - tbeg[g];
+  const long long e0 = lt * SCAN_TILE, len = gr.n + 1;
+  double acc = 0.0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    long long u = e0 + (long long)k * PLAN_THREADS + threadIdx.x;
+    if (u < len) acc += weight_at(gr, u);
+  }
+  double tot = block_reduce(acc);
+  if (threadIdx.x == 0) {
+    part[t] = tot;
+    head[t] = lt == 0;
+  }
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS) wprefix_scan_kernel(const DevGraph* __restrict__ gs,
+                                                                    const long long* __restrict__ tbeg, int G,
+                                                                    const double* __restrict__ part,
+                                                                    double* __restrict__ P) {
+  const long long t = blockIdx.x;
+  const int g = block_graph(tbeg, G, t);
+  const DevGraph& gr = gs[g];
+  const long long lt = t - tbeg[g];
+  const long long e0 = lt * SCAN_TILE, len = gr.n + 1;
+  // each thread owns SCAN_ITEMS consecutive elements
+  long long u0 = e0 + (long long)threadIdx.x * SCAN_ITEMS;
+  double v[SCAN_ITEMS];
+  double loc = 0.0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (u0 + k < len) ? weight_at(gr, u0 + k) : 0.0;
+    loc += v[k];
+  }
+  double tot;
+  double ex = block_excl_scan(loc, &tot) + part[t];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (u0 + k < len) P[gr.pbase + u0 + k] = ex;
+    ex += v[k];
+  }
+}
+
+void launch_weight_prefix(const DevGraph* d_graphs, const long long* d_tile_graph_begin, int G, long long ntiles,
+                          double* d_P, double* d_partials, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  unsigned char* head = (unsigned char*)(d_partials + ntiles);
+  wprefix_reduce_kernel<<<(unsigned)ntiles, PLAN_THREADS, 0, s>>>(d_graphs, d_tile_graph_begin, G, d_partials, head);
+  partials_scan_kernel<double><<<1, 1024, 0, s>>>(d_partials, ntiles, head);
+  wprefix_scan_kernel<<<(unsigned)ntiles, PLAN_THREADS, 0, s>>>(d_graphs, d_tile_graph_begin, G, d_partials, d_P);
+}
+
+// --------------------------------------------------------------- costs, Eq. 3
+// c_i = 1 + (w_u / S) * sum_{v in [j0, end)} w_v  (Eq. 1-2; for a light row
+// [u+1, n) this is Eq. 6: (w_u / S)(S - sigma_u - w_u) + 1).
+__global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __restrict__ gs, int G,
+                                                             long long n_items, const double* __restrict__ P,
+                                                             double* __restrict__ C) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n_items) return;
+  int g = G == 1 ? 0 : graph_of_item(gs, G, i);
+  const DevGraph& gr = gs[g];
+  unsigned u, seg, j0, end;
+  item_bounds(gr, i - gr.item_begin, u, seg, j0, end);
+  double wu = weight_at(gr, u);
+  const double* Pg = P + gr.pbase;
+  double S = gr.S_d > 0 ? gr.S_d : 1.0;
+  C[i] = 1.0 + wu / S * (Pg[end] - Pg[j0]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PLAN_THREADS) tile_reduce_kernel(const T* __restrict__ x, long long n,
+                                                                   T* __restrict__ part) {
+  long long e0 = blockIdx.x * (long long)SCAN_TILE;
+  T acc = T(0);
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    long long i = e0 + (long long)k * PLAN_THREADS + threadIdx.x;
+    if (i < n) acc += x[i];
+  }
+  T tot = block_reduce(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// in-place inclusive scan of doubles with tile partials
+__global__ void __launch_bounds__(PLAN_THREADS) tile_incl_scan_kernel(double* __restrict__ x, long long n,
+                                                                      const double* __restrict__ part) {
+  long long i0 = blockIdx.x * (long long)SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+  double v[SCAN_ITEMS];
+  double loc = 0.0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = i0 + k < n ? x[i0 + k] : 0.0;
+    loc += v[k];
+  }
+  double tot;
+  double run = block_excl_scan(loc, &tot) + part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    run += v[k];
+    if (i0 + k < n) x[i0 + k] = run;
+  }
+}
+
+// Eq. 3: task t starts at the first item with C_i >= t * Zbar, i.e. item i
+// starts the tasks floor(C_{i-1}/Zbar)+1 .. floor(C_i/Zbar) (the paper's
+// Find-Boundaries criterion floor(C_m/Zbar) != floor(C_{m+1}/Zbar)).
+__global__ void __launch_bounds__(PLAN_THREADS) task_bounds_kernel(const double* __restrict__ C, long long n_items,
+                                                                   long long* __restrict__ task_start, int T) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i == 0) {
+    task_start[0] = 0;
+    task_start[T] = n_items;
+  }
+  if (i >= n_items) return;
+  double Zbar = C[n_items - 1] / (double)T;
+  double qp = i > 0 ? C[i - 1] / Zbar : 0.0;
+  double q = C[i] / Zbar;
+  long long t0 = (long long)floor(qp) + 1, t1 = (long long)floor(q);
+  if (t1 > T - 1) t1 = T - 1;
+  for (long long t = t0; t <= t1; ++t) task_start[t] = i;
+}
+
+long long scan_partials_needed(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, const double* d_P, double* d_C,
+                            double* d_partials, long long* d_task_start, int T, cudaStream_t s) {
+  if (n_items <= 0) {
+    // empty plan: a single empty task
+    long long z[2] = {0, 0};
+    cudaMemcpyAsync(d_task_start, z, sizeof(z), cudaMemcpyHostToDevice, s);
+    return;
+  }
+  unsigned nb = (unsigned)((n_items + PLAN_THREADS - 1) / PLAN_THREADS);
+  costs_kernel<<<nb, PLAN_THREADS, 0, s>>>(d_graphs, G, n_items, d_P, d_C);
+  long long nt = (n_items + SCAN_TILE - 1) / SCAN_TILE;
+  tile_reduce_kernel<double><<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
+  partials_scan_kernel<double><<<1, 1024, 0, s>>>(d_partials, nt, nullptr);
+  tile_incl_scan_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
+  task_bounds_kernel<<<nb, PLAN_THREADS, 0, s>>>(d_C, n_items, d_task_start, T);
+}
+
+// --------------------------------------------------------------- count scan
+__global__ void __launch_bounds__(PLAN_THREADS) count_reduce_kernel(const int* __restrict__ x, long long n,
+                                                                    long long* __restrict__ part) {
+  long long e0 = blockIdx.x * (long long)SCAN_TILE;
+  long long acc = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    long long i = e0 + (long long)k * PLAN_THREADS + threadIdx.x;
+    if (i < n) acc += x[i];
+  }
+  long long tot = block_reduce(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS) count_scan_kernel(const int* __restrict__ x, long long n,
+                                                                  const long long* __restrict__ part,
+                                                                  long long* __restrict__ out, long long nt) {
+  long long i0 = blockIdx.x * (long long)SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS];
+  long long loc = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = i0 + k < n ? x[i0 + k] : 0;
+    loc += v[k];
+  }
+  long long tot;
+  long long run = block_excl_scan(loc, &tot) + part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (i0 + k < n) out[i0 + k] = run;
+    run += v[k];
+  }
+  if (blockIdx.x == nt - 1 && threadIdx.x == 0) out[n] = part[blockIdx.x] + tot;
+}
+
+void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, long long* d_partials,
+                       cudaStream_t s) {
+  if (n <= 0) {
+    cudaMemsetAsync(d_offsets, 0, sizeof(long long), s);
+    return;
+  }
+  long long nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  count_reduce_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_counts, n, d_partials);
+  partials_scan_kernel<long long><<<1, 1024, 0, s>>>(d_partials, nt, nullptr);
+  count_scan_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_counts, n, d_partials, d_offsets, nt);
+}
+
+}  // namespace cl

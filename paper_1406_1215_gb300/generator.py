@@ -1,0 +1,118 @@
+"""Convenience layer over the C ABI: owns the device buffers (torch tensors)
+that the library needs and calls the entry points in order.  All arithmetic
+runs in the CUDA library; this file only allocates and marshals.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import (CL_E_I32, CL_E_I64, CL_W_F64, CL_W_I32, HEAVY_W_DEFAULT, cl_count, cl_emit, cl_generate_batch,
+               cl_graph, cl_plan_build, cl_plan_create, cl_plan_destroy, cl_plan_graph_info, cl_plan_items,
+               cl_plan_scratch_bytes, cl_plan_workspace_bytes, cl_scan, cl_stats, cl_tuning)
+
+
+def _wtype(t: torch.Tensor) -> int:
+    if t.dtype == torch.int32:
+        return CL_W_I32
+    if t.dtype == torch.float64:
+        return CL_W_F64
+    raise TypeError("weights must be int32 or float64")
+
+
+class Generator:
+    """A plan over one or several graphs (sorted non-increasing weights on the
+    GPU, one seed each) with its workspace and count / offset buffers."""
+
+    def __init__(self, weights, seeds, heavy_w: float = HEAVY_W_DEFAULT, tasks: int = 0, block: int = 0,
+                 blocks_per_sm: int = 0, stream=None):
+        if isinstance(weights, torch.Tensor):
+            weights = [weights]
+            seeds = [seeds]
+        if len(weights) != len(seeds):
+            raise ValueError("one seed per graph")
+        for w in weights:
+            if not w.is_cuda or not w.is_contiguous():
+                raise ValueError("weights must be contiguous CUDA tensors")
+        self.weights = list(weights)
+        self.seeds = [int(s) for s in seeds]
+        self.G = len(self.weights)
+        self.device = self.weights[0].device
+        self.stream = stream
+        graphs = [cl_graph(w.numel(), _wtype(w), w.data_ptr(), s & (2**64 - 1), float(heavy_w))
+                  for w, s in zip(self.weights, self.seeds)]
+        tun = cl_tuning(tasks, block, blocks_per_sm)
+        sb = cl_plan_scratch_bytes(self.G)
+        scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+        self.plan = cl_plan_create(graphs, tun, scratch, sb, stream)
+        del scratch
+        wb = cl_plan_workspace_bytes(self.plan)
+        self.workspace = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        cl_plan_build(self.plan, self.workspace, wb, stream)
+        self.n_items = cl_plan_items(self.plan)
+        self.counts = torch.empty(max(self.n_items, 1), dtype=torch.int32, device=self.device)
+        self.offsets = torch.empty(self.n_items + 1, dtype=torch.int64, device=self.device)
+        self.m = None
+
+    def info(self, g: int = 0):
+        i = cl_plan_graph_info(self.plan, g)
+        return {"n": i.n, "H": i.H, "n_items": i.n_items, "item_begin": i.item_begin, "S_i64": i.S_i64,
+                "S": i.S, "status": i.status}
+
+    def count(self):
+        cl_count(self.plan, self.counts, self.stream)
+
+    def scan(self, want_total: bool = True):
+        m = cl_scan(self.plan, self.counts, self.offsets, want_total, self.stream)
+        if want_total:
+            self.m = m
+        return m
+
+    def emit(self, edges: torch.Tensor | None = None, etype: int = CL_E_I32, item_begin: int = 0,
+             item_end: int | None = None) -> torch.Tensor:
+        item_end = self.n_items if item_end is None else item_end
+        if edges is None:
+            if self.m is None:
+                self.scan(True)
+            dt = torch.int32 if etype == CL_E_I32 else torch.int64
+            edges = torch.empty((max(self.m, 1), 2), dtype=dt, device=self.device)
+        cap = edges.shape[0] if edges.numel() else 0
+        cl_emit(self.plan, self.offsets, etype, edges, cap, item_begin, item_end, self.stream)
+        return edges
+
+    def generate(self, etype: int = CL_E_I32) -> torch.Tensor:
+        """count -> scan (reads m back) -> emit; returns an (m, 2) tensor."""
+        self.count()
+        m = self.scan(True)
+        dt = torch.int32 if etype == CL_E_I32 else torch.int64
+        edges = torch.empty((max(m, 1), 2), dtype=dt, device=self.device)
+        self.emit(edges, etype)
+        return edges[:m]
+
+    def generate_batch(self, edges: torch.Tensor, graph_offsets: torch.Tensor, status: torch.Tensor,
+                       etype: int = CL_E_I32):
+        cap = edges.shape[0]
+        cl_generate_batch(self.plan, etype, edges, cap, graph_offsets, self.counts, self.offsets, status,
+                          self.stream)
+
+    def stats(self) -> dict:
+        return cl_stats(self.plan, self.stream)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            cl_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def generate(weights: torch.Tensor, seed: int, heavy_w: float = HEAVY_W_DEFAULT, etype: int = CL_E_I32):
+    """One graph: returns its (m, 2) edge list (u < v, canonical order)."""
+    g = Generator(weights, seed, heavy_w)
+    try:
+        return g.generate(etype)
+    finally:
+        g.close()
