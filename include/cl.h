@@ -189,6 +189,28 @@ cl_status cl_check(cl_plan* plan, cl_stream_t stream);
 
 void cl_plan_destroy(cl_plan* plan);
 
+/* --- for callers that cannot allocate device memory ----------------------
+ * The paper has no counterpart to this entry point: it exists for code that
+ * cannot call cudaMalloc -- a host callback or real-time loop that must not
+ * take cudaMalloc's implicit device synchronisation, a plug-in whose host
+ * framework owns all device memory, a fixed memory budget.
+ *
+ * cl_scan_noalloc computes exactly what cl_scan computes (d_offsets[i] =
+ * sum_{k<i} d_counts[k] for i = 0..n, d_offsets[n] = total, int64) without a
+ * plan or workspace and without allocating: its scratch (one int64 per 2048
+ * counts) is a fixed 1 MiB array inside the library, held on every GPU that
+ * loads the library until the process exits.  n must be <= 2^28
+ * (268,435,456); larger n returns CL_ERR_RANGE.  The first call on each
+ * device looks up that array's device address with the device current; make
+ * that first call before any stream capture.  All calls share the one array
+ * (its contents are rewritten by each call, nothing needs clearing), so two
+ * calls that may run at the same time on the GPU -- on different streams, or
+ * from different host threads -- race and corrupt each other's result:
+ * serialise them.  Asynchronous on `stream`; d_counts and d_offsets are
+ * caller-owned device arrays of n and n + 1 entries and must not overlap.
+ * Errors: CL_ERR_INVALID_ARG, CL_ERR_RANGE, CL_ERR_CUDA. */
+cl_status cl_scan_noalloc(const int32_t* d_counts, int64_t n, int64_t* d_offsets, cl_stream_t stream);
+
 /* --- diagnostics (exercise one primitive over arrays; for tests) ---------- */
 
 /* d_out[4i..4i+3] = Philox4x32-10(counter d_ctr[4i..4i+3], key (seed_lo, seed_hi)). */

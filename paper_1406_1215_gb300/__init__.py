@@ -85,6 +85,7 @@ def load_library(path: str | None = None):
         "cl_diag_philox_curand": ([vp, i64, u64, vp, vp], i32),
         "cl_diag_neglog": ([vp, vp, i64, vp, vp, vp], i32),
         "cl_diag_skip": ([vp, vp, vp, vp, i64, vp, vp, vp], i32),
+        "cl_scan_noalloc": ([vp, i64, vp, vp], i32),
     }
     optional = {
         "cl_expected_degree": ([vp, i64, ctypes.c_double, vp, vp], i32),
@@ -205,6 +206,13 @@ def cl_check(plan, stream=None) -> int:
 def cl_plan_destroy(plan):
     if plan:
         load_library().cl_plan_destroy(plan)
+
+
+def cl_scan_noalloc(d_counts, n: int, d_offsets, stream=None):
+    """cl_scan without a plan, a workspace or any allocation (for callers that
+    cannot allocate device memory); its scratch is a fixed array inside the
+    library, so concurrent calls race.  n <= 2^28."""
+    _check(load_library().cl_scan_noalloc(_ptr(d_counts), n, _ptr(d_offsets), _stream(stream)), "cl_scan_noalloc")
 
 
 def cl_diag_philox(d_ctr, count: int, seed: int, d_out, stream=None):
