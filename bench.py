@@ -30,11 +30,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "edges/sec on 1 GB300 and % of HBM write roofline; batched graphs/sec; calibrate s"
-WORKLOAD = "pl_n1e8"
-CONFIG = {"workload": "chung-lu power law n=1e8, gamma=2.3, degrees [20,1e5], degree seed 3, edge seed 42, "
-                      "int32 edge pairs", "n": 100_000_000, "gamma": 2.3, "dmin": 20, "dmax": 100_000,
-          "heavy_w": 8192.0, "segment": 65536, "etype": "int32 pairs",
-          "l2": "inputs (400 MB weights) and outputs (~31 GB edges) exceed the 129 MB L2; no flush needed"}
+WORKLOADS = {
+    "pl_n1e8": {"workload": "chung-lu power law n=1e8, gamma=2.3, degrees [20,1e5], degree seed 3, edge seed 42, "
+                            "int32 edge pairs", "n": 100_000_000, "gamma": 2.3, "dmin": 20, "dmax": 100_000},
+    "pl_n1e7": {"workload": "chung-lu power law n=1e7, gamma=2.5, degrees [10,1e4], degree seed 2, edge seed 42, "
+                            "int32 edge pairs (profiling case)", "n": 10_000_000, "gamma": 2.5, "dmin": 10,
+                "dmax": 10_000},
+    "er_n1e8": {"workload": "chung-lu constant weights w=100 (Erdos-Renyi p=1e-6), n=1e8, edge seed 42, "
+                            "int32 edge pairs", "n": 100_000_000},
+}
+COMMON = {"heavy_w": 8192.0, "segment": 65536, "etype": "int32 pairs",
+          "l2": "inputs (weights, >= 40 MB) and outputs (>= 1 GB edges) exceed the 129 MB L2 between steps; "
+                "no flush"}
 KERNELS_PER_STEP = 14  # analyze 1 + weight prefix 3 + costs/scan/tasks 5 + count 1 + count scan 3 + emit 1
 
 
@@ -112,7 +119,7 @@ def run_reference(args, rank: int, world: int):
         return
     from paper_1406_1215_gb300 import inputs
 
-    w, seed = inputs.workload(WORKLOAD)
+    w, seed = inputs.workload(args.workload)
     per_step = []
     for s in range(args.warmup + args.steps):
         cb = cpu_baseline(w, seed, budget_s=4.0)
@@ -121,7 +128,8 @@ def run_reference(args, rank: int, world: int):
     v = statistics.mean(per_step)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64/binary128", "data": "synthetic", "config": CONFIG,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/binary128", "data": "synthetic",
+            "config": dict(WORKLOADS[args.workload], **COMMON),
             "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
                              "sample": "per step: random ranges of 2000 items of the workload, ~4 s of CPU"},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -146,16 +154,17 @@ def run_ours(args, rank: int, world: int):
     if world > 1:
         import torch.distributed as dist
 
-    w_np, seed = inputs.workload(WORKLOAD)
+    w_np, seed = inputs.workload(args.workload)
     seed = seed + rank
     n = len(w_np)
     w = torch.from_numpy(w_np).to(dev)
     graph = P.cl_graph(n, P.CL_W_I32, w.data_ptr(), seed, 8192.0)
     sb = P.cl_plan_scratch_bytes(1)
     scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+    tun = P.cl_tuning(0, 0, 0, 1 if args.no_stage else 0, 0.0)
 
     # sizes from one untimed pass
-    plan = P.cl_plan_create([graph], None, scratch, sb, sh)
+    plan = P.cl_plan_create([graph], tun, scratch, sb, sh)
     wb = P.cl_plan_workspace_bytes(plan)
     ws = torch.empty(wb, dtype=torch.uint8, device=dev)
     P.cl_plan_build(plan, ws, wb, sh)
@@ -172,7 +181,7 @@ def run_ours(args, rank: int, world: int):
     kern = {"count": [], "emit": []}
 
     def step(timed_kernels: bool):
-        pl = P.cl_plan_create([graph], None, scratch, sb, sh)
+        pl = P.cl_plan_create([graph], tun, scratch, sb, sh)
         P.cl_plan_build(pl, ws, wb, sh)
         e0, e1, e2, e3 = ev(), ev(), ev(), ev()
         e0.record(stream)
@@ -234,7 +243,7 @@ def run_ours(args, rank: int, world: int):
 
         def e2e_step():
             w_dev.copy_(w_host, non_blocking=True)
-            pl = P.cl_plan_create([graph2], None, scratch, sb, sh)
+            pl = P.cl_plan_create([graph2], tun, scratch, sb, sh)
             P.cl_plan_build(pl, ws, wb, sh)
             P.cl_count(pl, counts, sh)
             mm = P.cl_scan(pl, counts, offsets, True, sh)
@@ -260,7 +269,8 @@ def run_ours(args, rank: int, world: int):
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32x2", "data": "synthetic", "config": CONFIG,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32x2", "data": "synthetic",
+        "config": dict(WORKLOADS[args.workload], **COMMON),
         "edges_per_step": m_step,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "sample_kernel<emit,int2>", "peak_source": how,
@@ -284,6 +294,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="pl_n1e8", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-stage", action="store_true", help="count-only first pass; emit regenerates")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -84,8 +84,15 @@ typedef struct {
 /* Performance knobs only: no choice changes any output bit. */
 typedef struct {
   int32_t tasks;         /* number of equal-cost tasks (Eq. 3 partitions); 0 = automatic */
-  int32_t block;         /* threads per block of the sampler kernels, multiple of 32; 0 = 256 */
+  int32_t block;         /* threads per block of the sampler kernels, multiple of 32, <= 256; 0 = 256 */
   int32_t blocks_per_sm; /* resident blocks per SM for the persistent sampler grid; 0 = automatic */
+  int32_t no_stage;      /* 1: cl_count only counts and cl_emit regenerates every item (smaller
+                          * workspace, twice the sampling work); 0: cl_count also stages each
+                          * item's destinations in a slot of e + 4 sqrt(e) + 8 entries (e = the
+                          * item's uncapped expected edges, Eq. 1) and cl_emit copies them;
+                          * items that outgrow their slot are regenerated by cl_emit */
+  double stage_factor;   /* 0; a negative value shrinks every slot to 8 entries, so that most
+                          * items take the regeneration path (for testing that path) */
 } cl_tuning;
 
 typedef struct {
@@ -147,7 +154,10 @@ cl_status cl_plan_graph_info(const cl_plan* plan, int32_t g, cl_graph_info* out)
 /* --- sampling (Algorithm 1, Create-Edges, per item) ---------------------- */
 
 /* Count pass: d_counts[i] = number of edges of global item i (int32, n_items
- * entries, caller-owned).  Asynchronous. */
+ * entries, caller-owned).  Unless the tuning disabled staging, the pass also
+ * stores each item's destination nodes, in order, in the plan workspace, so
+ * that cl_emit only has to copy them (the sampling arithmetic runs once).
+ * Asynchronous. */
 cl_status cl_count(cl_plan* plan, int32_t* d_counts, cl_stream_t stream);
 
 /* Exclusive scan of the counts: d_offsets[i] = sum_{k<i} d_counts[k] for
@@ -158,7 +168,9 @@ cl_status cl_count(cl_plan* plan, int32_t* d_counts, cl_stream_t stream);
 cl_status cl_scan(cl_plan* plan, const int32_t* d_counts, int64_t* d_offsets, int64_t* h_total,
                   cl_stream_t stream);
 
-/* Emit pass: regenerates items [item_begin, item_end) and writes edge k of
+/* Emit pass: writes the edges of items [item_begin, item_end) -- copied from
+ * the staging of the last cl_count when there is one, otherwise (and for items
+ * that did not fit in the staging pool) regenerated -- edge k of
  * item i to d_edges[d_offsets[i] - d_offsets[item_begin] + k] as a (u, v)
  * pair of etype (CL_E_I32: 2 x int32 = 8 bytes; CL_E_I64: 2 x int64 = 16
  * bytes), u < v, local vertex ids of the item's graph.  capacity = edges that

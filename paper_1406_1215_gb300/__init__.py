@@ -38,7 +38,8 @@ class cl_graph(ctypes.Structure):
 
 
 class cl_tuning(ctypes.Structure):
-    _fields_ = [("tasks", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+    _fields_ = [("tasks", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("no_stage", ctypes.c_int32), ("stage_factor", ctypes.c_double)]
 
 
 class cl_graph_info(ctypes.Structure):

@@ -28,6 +28,10 @@ struct cl_plan {
   int block = 256;
   int grid_count = 0, grid_emit32 = 0, grid_emit64 = 0;
   long long max_n = 0;
+  bool stage = true;                  // cl_count stages destinations
+  unsigned long long pool_cap = 0;    // staging pool entries
+  bool staged = false;                // the last cl_count staged (cl_emit copies)
+  bool tiny_slots = false;            // testing knob: 8-entry slots (most items regenerate)
   // workspace (after cl_plan_build)
   bool built = false;
   size_t ws_bytes = 0;
@@ -41,6 +45,10 @@ struct cl_plan {
   unsigned* d_ctr = nullptr;
   int* d_err = nullptr;
   unsigned long long* d_stats = nullptr;
+  unsigned* d_pool = nullptr;
+  int* d_slot32 = nullptr;
+  long long* d_slot_base = nullptr;
+  int* d_overflow = nullptr;
 };
 
 namespace {
@@ -102,6 +110,10 @@ struct WsLayout {
   unsigned* ctr;
   int* err;
   unsigned long long* stats;
+  int* overflow;
+  int* slot32;
+  long long* slot_base;
+  unsigned* pool;
   size_t bytes;
 };
 
@@ -120,6 +132,10 @@ WsLayout ws_layout(void* base, const cl_plan* p) {
   L.ctr = c.take<unsigned>(4);
   L.err = c.take<int>(4);
   L.stats = c.take<unsigned long long>(4);
+  L.overflow = c.take<int>(4);
+  L.slot32 = p->stage ? c.take<int>(p->n_items > 0 ? p->n_items : 1) : nullptr;
+  L.slot_base = p->stage ? c.take<long long>(p->n_items + 1) : nullptr;
+  L.pool = p->stage ? c.take<unsigned>(p->pool_cap > 0 ? p->pool_cap : 1) : nullptr;
   L.bytes = c.off;
   return L;
 }
@@ -134,6 +150,9 @@ DevPlan dev_plan(const cl_plan* p) {
   P.task_ctr = p->d_ctr;
   P.err = p->d_err;
   P.stats = p->d_stats;
+  P.pool = p->d_pool;
+  P.slot_base = p->d_slot_base;
+  P.overflow = p->d_overflow;
   return P;
 }
 
@@ -249,6 +268,9 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     } else {
       d.S_i = (long long)res[g].S_i;
       d.S_d = (double)d.S_i;
+      float hi = (float)d.S_i;  // float-float split of S for the per-candidate arithmetic
+      d.S_ff_hi = hi;
+      d.S_ff_lo = (float)(d.S_i - (long long)hi);
       if (gs == CL_OK && res[g].S_i >= (1ull << 53)) gs = CL_ERR_RANGE;
     }
     d.H = (long long)res[g].H;
@@ -298,6 +320,21 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
   p->grid_emit32 = p->sms * (bps_e32 > 0 ? bps_e32 : 1);
   p->grid_emit64 = p->sms * (bps_e64 > 0 ? bps_e64 : 1);
   long long warps = (long long)p->grid_count * (p->block / 32);
+  // staging pool: item slots of e_i + 4 sqrt(e_i) + 8 entries (rounded up to 8), e_i the
+  // uncapped expected edges of item i, sum_i e_i = (S^2 - sum w^2) / (2 S); by
+  // Cauchy-Schwarz sum_i sqrt(e_i) <= sqrt(items * sum_i e_i), so this bounds the pool
+  p->stage = !(tuning && tuning->no_stage);
+  p->tiny_slots = tuning && tuning->stage_factor < 0;
+  if (p->stage) {
+    double em = 0;
+    for (int g = 0; g < G; ++g) {
+      double S = p->dg[g].S_d;
+      if (S > 0) em += (S * S - res[g].S2) / (2.0 * S);
+    }
+    if (em < 0) em = 0;
+    double cap = em + 4.0 * std::sqrt((double)items * em) + 16.0 * (double)items + 64.0;
+    p->pool_cap = (unsigned long long)cap;
+  }
   long long T = (tuning && tuning->tasks > 0) ? tuning->tasks : 16 * warps;
   long long cap = (items + 31) / 32;
   if (T > cap) T = cap;
@@ -330,6 +367,10 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   p->d_ctr = L.ctr;
   p->d_err = L.err;
   p->d_stats = L.stats;
+  p->d_pool = L.pool;
+  p->d_slot32 = L.slot32;
+  p->d_slot_base = L.slot_base;
+  p->d_overflow = L.overflow;
   cl_status st;
   if ((st = cuda_ok(cudaMemcpyAsync(L.graphs, p->dg.data(), sizeof(DevGraph) * p->G, cudaMemcpyHostToDevice, s))))
     return st;
@@ -339,8 +380,11 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   if ((st = cuda_ok(cudaMemsetAsync(L.ctr, 0, 4 * sizeof(unsigned) + 0, s)))) return st;
   if ((st = cuda_ok(cudaMemsetAsync(L.err, 0, 4 * sizeof(int), s)))) return st;
   if ((st = cuda_ok(cudaMemsetAsync(L.stats, 0, 4 * sizeof(unsigned long long), s)))) return st;
+  if ((st = cuda_ok(cudaMemsetAsync(L.overflow, 0, 4 * sizeof(int), s)))) return st;
   launch_weight_prefix(L.graphs, L.tile_begin, p->G, p->ntiles, L.P, L.part, s);
-  launch_costs_and_tasks(L.graphs, p->G, p->n_items, L.P, L.C, L.part, L.task, p->T, s);
+  launch_costs_and_tasks(L.graphs, p->G, p->n_items, L.P, L.C, L.part, L.task, p->T, L.slot32, p->tiny_slots ? 1 : 0,
+                         s);
+  if (p->stage) launch_count_scan(L.slot32, p->n_items, L.slot_base, L.scan_part, s);  // slot bases
   if ((st = last_ok())) return st;
   p->built = true;
   return CL_OK;
@@ -364,7 +408,8 @@ cl_status cl_count(cl_plan* p, int32_t* d_counts, cl_stream_t stream) {
   if (p->n_items == 0) return CL_OK;
   cudaStream_t s = (cudaStream_t)stream;
   cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s);
-  launch_count(dev_plan(p), d_counts, p->block, p->grid_count, s);
+  launch_count(dev_plan(p), p->G == 1 ? &p->dg[0] : nullptr, d_counts, p->stage, p->block, p->grid_count, s);
+  p->staged = p->stage;
   return last_ok();
 }
 
@@ -392,8 +437,8 @@ cl_status cl_emit(cl_plan* p, const int64_t* d_offsets, int32_t etype, void* d_e
   if (!p->built) return CL_ERR_STATE;
   if (item_end == item_begin) return CL_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  launch_emit(dev_plan(p), (const long long*)d_offsets, item_begin, item_end, etype, d_edges, capacity, p->block,
-              etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, s);
+  launch_emit(dev_plan(p), p->G == 1 ? &p->dg[0] : nullptr, (const long long*)d_offsets, item_begin, item_end, etype,
+              d_edges, capacity, p->staged, p->block, etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, s);
   return last_ok();
 }
 
@@ -412,8 +457,8 @@ cl_status cl_generate_batch(cl_plan* p, int32_t etype, void* d_edges, int64_t ca
                        capacity, d_status, s);
   if ((st = last_ok())) return st;
   if (p->n_items == 0) return CL_OK;
-  launch_emit(dev_plan(p), (const long long*)d_offsets, 0, p->n_items, etype, d_edges, capacity, p->block,
-              etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, s);
+  launch_emit(dev_plan(p), p->G == 1 ? &p->dg[0] : nullptr, (const long long*)d_offsets, 0, p->n_items, etype,
+              d_edges, capacity, p->staged, p->block, etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, s);
   return last_ok();
 }
 

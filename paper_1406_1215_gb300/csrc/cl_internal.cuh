@@ -26,6 +26,7 @@ struct DevGraph {
   long long n_items;      // items of this graph
   long long pbase;        // offset of this graph's weight prefix (n + 1 entries)
   int wtype;              // cl_wtype
+  float S_ff_hi, S_ff_lo; // S as float-float (integer weights)
   int pad_;
 };
 
@@ -36,6 +37,7 @@ struct GraphAnalysis {
   unsigned int flags;           // bit 0: unsorted, bit 1: negative / non-finite
   unsigned int pad_;
   double S_d;                   // correctly rounded sum (double weights)
+  double S2;                    // sum of w^2 (sizes the staging pool only)
 };
 
 // Items of heavy rows [0, U): sum_{u<U} K_u, K_u = N1 - ((u+1) >> 16) + 1,
@@ -97,6 +99,9 @@ struct DevPlan {
   unsigned* task_ctr;           // dynamic task counter (reset before each sampler launch)
   int* err;                     // device error word (first error wins)
   unsigned long long* stats;    // iterations, fallbacks, ties
+  unsigned* pool;               // staging pool of destination nodes
+  const long long* slot_base;   // per item: first pool entry of its slot (n_items + 1 entries)
+  int* overflow;                // set when an item outgrew its slot
 };
 
 // ---- launchers implemented in plan.cu / sample.cu / diag.cu ----
@@ -111,17 +116,21 @@ size_t f64_bins_bytes(int G);
 // Weight prefix P_g[u] = sum_{v<u} w_v for u = 0..n_g (as double), tile-segmented by graph.
 void launch_weight_prefix(const DevGraph* d_graphs, const long long* d_tile_graph_begin, int G, long long ntiles,
                           double* d_P, double* d_partials, cudaStream_t s);
-// Item costs c_i, inclusive prefix C in place, task boundaries (Eq. 3).
+// Item costs c_i, inclusive prefix C in place, task boundaries (Eq. 3); when d_slot32
+// is given, also the staging slot sizes (8-aligned, int32) of every item.
 void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, const double* d_P, double* d_C,
-                            double* d_partials, long long* d_task_start, int T, cudaStream_t s);
+                            double* d_partials, long long* d_task_start, int T, int* d_slot32, int tiny_slots,
+                            cudaStream_t s);
 // Exclusive int32 -> int64 scan with the total at out[n].
 void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, long long* d_partials,
                        cudaStream_t s);
 long long scan_partials_needed(long long n);
 
-void launch_count(const DevPlan& P, int* d_counts, int block, int grid, cudaStream_t s);
-void launch_emit(const DevPlan& P, const long long* d_offsets, long long ib, long long ie, int etype, void* d_edges,
-                 long long capacity, int block, int grid, cudaStream_t s);
+// `single`: host copy of the plan's only graph (G == 1), passed to the kernels by value; else nullptr
+void launch_count(const DevPlan& P, const DevGraph* single, int* d_counts, bool stage, int block, int grid,
+                  cudaStream_t s);
+void launch_emit(const DevPlan& P, const DevGraph* single, const long long* d_offsets, long long ib, long long ie,
+                 int etype, void* d_edges, long long capacity, bool staged, int block, int grid, cudaStream_t s);
 void launch_graph_offsets(const DevGraph* d_graphs, int G, const long long* d_offsets, long long n_items,
                           long long* d_graph_offsets, long long capacity, int* d_status, cudaStream_t s);
 int sampler_max_blocks_per_sm(int block, bool emit, int etype);

@@ -57,6 +57,12 @@ __device__ __forceinline__ ff ff_add(ff x, ff y) {
   s.lo = __fadd_rn(s.lo, t.lo);
   return ff_fast_two_sum(s.hi, s.lo);
 }
+// Dekker's add: error <= ~2^-47 (|x| + |y|); used where |x + y| >= (|x| + |y|) / 4
+__device__ __forceinline__ ff ff_add_fast(ff x, ff y) {
+  ff s = ff_two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return ff_fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ ff ff_mul(ff x, ff y) {
   ff p = ff_two_prod(x.hi, y.hi);
@@ -83,11 +89,47 @@ __device__ __forceinline__ ff ff_div(ff x, ff y) {
   float q2 = __fmul_rn(e, r);
   return ff_fast_two_sum(q1, q2);
 }
-// signed 64-bit integer (|v| < 2^62) to float-float, ~48 significant bits
+// ---- integer -> float without conversion instructions.  On this GPU the
+// int<->float conversion instructions share the slow FP64-class pipe, so the
+// per-candidate path builds floats from integer bits instead: for
+// 0 <= x < 2^23 the float with biased exponent 150 and significand bits x is
+// exactly 2^23 + x.
+__device__ __forceinline__ float u23_to_f(unsigned x) {
+  return __fsub_rn(__int_as_float(0x4B000000u | x), 8388608.0f);
+}
+// unsigned 64-bit integer to float-float: three exact 23-bit chunks, summed
+// with one error-free TwoSum; exact below 2^46, relative error < 2^-47 above.
+__device__ __forceinline__ ff ff_from_u64(unsigned long long x) {
+  float f2 = __fmul_rn(u23_to_f((unsigned)(x >> 46)), 0x1p46f);
+  float f1 = __fmul_rn(u23_to_f((unsigned)(x >> 23) & 0x7FFFFFu), 0x1p23f);
+  float f0 = u23_to_f((unsigned)x & 0x7FFFFFu);
+  ff s = ff_two_sum(f2, f1);
+  s.lo = __fadd_rn(s.lo, f0);
+  return ff_fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ ff ff_from_i64(long long v) {
-  float hi = __ll2float_rn(v);
-  float lo = __ll2float_rn(v - __float2ll_rz(hi));
-  return {hi, lo};
+  ff r = ff_from_u64((unsigned long long)(v < 0 ? -v : v));
+  return v < 0 ? ff{-r.hi, -r.lo} : r;
+}
+
+// 2 atanh(s) and the table/exponent terms shared by the two reductions:
+// returns e ln2 + ln(64/J) - 2 atanh(s).
+__device__ __forceinline__ ff ff_reduce_tail(ff s, int e, int J) {
+  // atanh(s) = s (1 + z (1/3 + z/5 + z^2/7 + z^3/9)), z = s^2, |s| <~ 2^-7
+  ff z = ff_two_prod(s.hi, s.hi);
+  z.lo = fmaf(2.0f * s.hi, s.lo, z.lo);
+  z = ff_fast_two_sum(z.hi, z.lo);
+  float tail = z.hi * fmaf(z.hi, fmaf(z.hi, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f);
+  // 1/3 + tail: tail < 2^-14, its float rounding is far below the target
+  ff P2 = ff_fast_two_sum(CL_THIRD_FF_HI, __fadd_rn(tail, CL_THIRD_FF_LO));
+  ff c = ff_mul(z, P2);        // z (1/3 + ...)
+  ff sc = ff_mul(s, c);        // s z (...), |sc| < 2^-14 |s|
+  ff at = ff_add_fast(s, sc);  // atanh(s)
+  ff t = ff{__ldg(&CL_LNT_FF[J - 32][0]), __ldg(&CL_LNT_FF[J - 32][1])};
+  ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f((unsigned)e));
+  ff r = ff_add_fast(le, t);  // both >= 0
+  // r - 2 atanh(s) >= (r + |2 atanh(s)|) / 4 (|2 atanh s| <~ r for J < 64; r = 0 for J = 64)
+  return ff_add_fast(r, ff{-2.0f * at.hi, -2.0f * at.lo});
 }
 
 // -ln(A / B) for integers 1 <= A < B <= 2^55, as float-float.
@@ -98,29 +140,41 @@ __device__ __forceinline__ ff ff_neglog_ratio(unsigned long long A, unsigned lon
     Ap >>= 1;
     e -= 1;
   }
-  // J = round(64 A'/B) from the top 24 bits (an off-by-one J only widens |s| slightly)
-  int sh = 40 - __clzll(B);
+  // J = round(64 A'/B) from the top 23 bits (an off-by-one J only widens |s| slightly)
+  int sh = 41 - __clzll(B);
   sh = sh < 0 ? 0 : sh;
-  float fa = __uint2float_rn((unsigned)(Ap >> sh));
-  float fb = __uint2float_rn((unsigned)(B >> sh));
-  int J = __float2int_rn(__fdividef(64.0f * fa, fb));
+  float q = 64.0f * u23_to_f((unsigned)(Ap >> sh)) * __frcp_rn(u23_to_f((unsigned)(B >> sh)));
+  int J = __float_as_int(__fadd_rn(q, 12582912.0f)) - 0x4B400000;  // round to nearest
   J = J < 32 ? 32 : (J > 64 ? 64 : J);
   long long N = (long long)(Ap << 6) - (long long)J * (long long)B;
   long long D = (long long)(Ap << 6) + (long long)J * (long long)B;
-  ff s = ff_div(ff_from_i64(N), ff_from_i64(D));
-  // atanh(s) = s (1 + z (1/3 + z/5 + z^2/7 + z^3/9)), z = s^2
-  ff z = ff_two_prod(s.hi, s.hi);
-  z.lo = fmaf(2.0f * s.hi, s.lo, z.lo);
-  z = ff_fast_two_sum(z.hi, z.lo);
-  float tail = z.hi * fmaf(z.hi, fmaf(z.hi, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f);
-  ff P2 = ff_add(ff{CL_THIRD_FF_HI, CL_THIRD_FF_LO}, ff{tail, 0.0f});
-  ff c = ff_mul(z, P2);   // z (1/3 + ...)
-  ff sc = ff_mul(s, c);   // s z (...)
-  ff at = ff_add(s, sc);  // atanh(s)
-  ff t = ff{__ldg(&CL_LNT_FF[J - 32][0]), __ldg(&CL_LNT_FF[J - 32][1])};
-  ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, (float)e);
-  ff r = ff_add(le, t);
-  return ff_add(r, ff{-2.0f * at.hi, -2.0f * at.lo});
+  return ff_reduce_tail(ff_div(ff_from_i64(N), ff_from_u64((unsigned long long)D)), e, J);
+}
+
+// -ln r for r = A / 2^53, A odd in [1, 2^53): the reduction needs no division
+// to pick J (B is a power of two) and s = N / (J 2^48 + N), N = A' - J 2^47.
+__device__ __forceinline__ ff ff_neglog_r53(unsigned long long A) {
+  int e = __clzll(A) - 11;
+  unsigned long long Ap = A << e;                      // [2^52, 2^53)
+  int J = (int)((Ap + (1ull << 46)) >> 47);            // [32, 64]
+  long long N = (long long)Ap - ((long long)J << 47);  // [-2^46, 2^46]
+  ff Nf = ff_from_i64(N);
+  ff Df = ff_add_fast(ff{__fmul_rn(u23_to_f((unsigned)J), 0x1p48f), 0.0f}, Nf);  // |N| <= J 2^48 / 64
+  return ff_reduce_tail(ff_div(Nf, Df), e, J);
+}
+
+// -ln(1 - Q/S) for integers 0 < Q < S <= 2^48.  For p = Q/S < 2^-12 the series
+// p (1 + p/2 + p^2/3 + p^3/4 + p^4/5) (next term < 2^-50 relative); otherwise
+// the table reduction of -ln((S - Q) / S).
+__device__ __forceinline__ ff ff_neglog1m(unsigned long long Q, unsigned long long S, ff Sf) {
+  if (Q < (S >> 12)) {
+    ff p = ff_div(ff_from_u64(Q), Sf);
+    float t = p.hi * p.hi * fmaf(p.hi, fmaf(p.hi, 0.2f, 0.25f), 1.0f / 3.0f);
+    ff c = ff_fast_two_sum(1.0f, 0.5f * p.hi);
+    c.lo = __fadd_rn(c.lo, __fadd_rn(0.5f * p.lo, t));
+    return ff_mul(p, c);
+  }
+  return ff_neglog_ratio(S - Q, S);
 }
 
 // ------------------------------------------------------------- double-double
@@ -204,6 +258,20 @@ __device__ __forceinline__ dd dd_neglog_ratio(unsigned long long A, unsigned lon
 // Outcome of one tier: the floor of x clamped at R, or "undecided".
 static constexpr long long SKIP_UNDECIDED = -1;
 
+// floor of 0 <= x < 2^33 as an integer and as a float, from the float's bits
+// (no conversion instructions): below 2^23, x + 2^23 rounded down is
+// 2^23 + floor(x); above, x is an integer whose significand is shifted out.
+__device__ __forceinline__ long long floor_f(float x, float* fl) {
+  if (x < 0x1p23f) {
+    float t = __fadd_rd(x, 0x1p23f);
+    *fl = __fsub_rn(t, 0x1p23f);
+    return (long long)(__float_as_int(t) - 0x4B000000);
+  }
+  *fl = x;
+  unsigned b = __float_as_uint(x);
+  return (long long)((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u);
+}
+
 // x = hi + lo >= 0: floor(x) clamped at R, when x is farther than
 // margin = tau * x from every integer (tau = 2^-40 for float-float).
 // x - k0 (k0 = floor(hi)) is formed exactly; the distances of x to floor(x)
@@ -211,27 +279,30 @@ static constexpr long long SKIP_UNDECIDED = -1;
 // is safe whenever the evaluation error of x is below margin / 2.
 __device__ __forceinline__ long long floor_decide_ff(ff x, long long R) {
   const float tau = 0x1p-40f;
-  if (x.hi > 0x1p33f || x.hi > (float)R * (1.0f + 0x1p-20f)) return R;  // x >= R for sure
-  float k0 = floorf(x.hi);
-  ff r = ff_two_sum(__fsub_rn(x.hi, k0), x.lo);  // x - k0, exact, in (-1/2, 1)
+  if (!(x.hi < 0x1p33f)) return R;  // x >= 2^33 > R for sure
+  float k0f;
+  long long k0 = floor_f(x.hi, &k0f);
+  if (k0 > R) return R;  // x >= R + 1 (1 - 2^-43) > R: the item ends, no window needed
+  ff r = ff_two_sum(__fsub_rn(x.hi, k0f), x.lo);  // x - k0, exact, in (-1/2, 1)
   long long k;
   float dlo, dhi;  // distances from x to k and to k + 1
   if (r.hi < 0.0f) {  // x just below k0 (x.hi integral, x.lo < 0)
-    k = (long long)k0 - 1;
+    k = k0 - 1;
     dhi = __fsub_rn(-r.hi, r.lo);
     dlo = __fadd_rn(1.0f, r.hi);
   } else if (r.hi > 1.0f || (r.hi == 1.0f && r.lo >= 0.0f)) {
-    k = (long long)k0 + 1;
+    k = k0 + 1;
     dlo = __fadd_rn(__fsub_rn(r.hi, 1.0f), r.lo);
     dhi = __fsub_rn(1.0f, dlo);
   } else {
-    k = (long long)k0;
+    k = k0;
     dlo = __fadd_rn(r.hi, r.lo);
     dhi = __fsub_rn(__fsub_rn(1.0f, r.hi), r.lo);
   }
   float margin = tau * x.hi;
+  if (k >= R) return dlo > margin ? R : SKIP_UNDECIDED;  // only x >= R matters
   if (!(dlo > margin) || !(dhi > margin)) return SKIP_UNDECIDED;
-  return k < R ? k : R;
+  return k;
 }
 
 // Same for double-double with tau = 2^-96; an undecided x takes the nearest

@@ -44,7 +44,8 @@ __global__ void diag_neglog_kernel(const unsigned long long* __restrict__ A, con
     odd[2 * i] = odd[2 * i + 1] = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
-  ff f = ff_neglog_ratio(A[i], B[i]);
+  // the float-float forms the sampler uses: -ln r (B = 2^53) or -ln(1 - Q/S)
+  ff f = B[i] == (1ull << 53) ? ff_neglog_r53(A[i]) : ff_neglog1m(B[i] - A[i], B[i], ff_from_u64(B[i]));
   dd d = dd_neglog_ratio(A[i], B[i]);
   oft[2 * i] = f.hi;
   oft[2 * i + 1] = f.lo;
@@ -64,8 +65,8 @@ __global__ void diag_skip_kernel(const unsigned long long* __restrict__ a, const
     return;
   }
   unsigned long long Ar = 2ull * a[i] + 1ull;
-  ff Lr = ff_neglog_ratio(Ar, 1ull << 53);
-  ff Lp = ff_neglog_ratio(S[i] - Q[i], S[i]);
+  ff Lr = ff_neglog_r53(Ar);
+  ff Lp = ff_neglog1m(Q[i], S[i], ff_from_u64(S[i]));
   long long d = floor_decide_ff(ff_div(Lr, Lp), R[i]);
   int tr = 0;
   if (d == SKIP_UNDECIDED) {

@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) analyze_kernel(const DevGraph* _
   long long i1 = i0 + ANALYZE_CHUNK < n ? i0 + ANALYZE_CHUNK : n;
   unsigned flags = 0;
   unsigned long long heavy = 0, sum = 0;
+  double sq = 0.0;
   if (F64) {
     for (int k = threadIdx.x; k < 2 * F64_BINS; k += blockDim.x) sbins[k] = 0;
     __syncthreads();
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) analyze_kernel(const DevGraph* _
       }
       if (i + 1 < n && x < w[i + 1]) flags |= 1u;
       if (x >= hw) ++heavy;
+      sq += x * x;
       unsigned long long bits = (unsigned long long)__double_as_longlong(x);
       int e = (int)(bits >> 52);
       unsigned long long m = bits & ((1ull << 52) - 1);
@@ -183,17 +185,20 @@ __global__ void __launch_bounds__(PLAN_THREADS) analyze_kernel(const DevGraph* _
       if (i + 1 < n && x < w[i + 1]) flags |= 1u;
       if ((double)x >= hw) ++heavy;
       sum += (unsigned long long)(long long)x;
+      sq += (double)x * (double)x;
     }
   }
   // block reductions
   unsigned long long s = block_reduce(sum);
   unsigned long long h = block_reduce(heavy);
+  double q2 = block_reduce(sq);
   unsigned f1 = __syncthreads_or(flags & 1u) ? 1u : 0u;
   unsigned f2 = __syncthreads_or(flags & 2u) ? 2u : 0u;
   unsigned f = f1 | f2;
   if (threadIdx.x == 0) {
     if (!F64 && s) atomicAdd(&out[g].S_i, s);
     if (h) atomicAdd(&out[g].H, h);
+    if (q2 > 0.0) atomicAdd(&out[g].S2, q2);
     if (f) atomicOr(&out[g].flags, f);
   }
 }
@@ -350,7 +355,8 @@ void launch_weight_prefix(const DevGraph* d_graphs, const long long* d_tile_grap
 // [u+1, n) this is Eq. 6: (w_u / S)(S - sigma_u - w_u) + 1).
 __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __restrict__ gs, int G,
                                                              long long n_items, const double* __restrict__ P,
-                                                             double* __restrict__ C) {
+                                                             double* __restrict__ C, int* __restrict__ slot,
+                                                             int tiny_slots) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n_items) return;
   int g = G == 1 ? 0 : graph_of_item(gs, G, i);
@@ -360,7 +366,16 @@ __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __r
   double wu = weight_at(gr, u);
   const double* Pg = P + gr.pbase;
   double S = gr.S_d > 0 ? gr.S_d : 1.0;
-  C[i] = 1.0 + wu / S * (Pg[end] - Pg[j0]);
+  double e = wu / S * (Pg[end] - Pg[j0]);  // expected edges of the item (uncapped)
+  C[i] = 1.0 + e;
+  if (slot) {
+    // staging slot: e + 4 sd + 8 entries in whole sectors, at most the item's length
+    double want = tiny_slots ? 8.0 : e + 4.0 * sqrt(e) + 8.0;
+    double len = (double)(end - j0);
+    if (want > len) want = len;
+    if (want > 1e9) want = 1e9;
+    slot[i] = ((int)ceil(want) + 7) & ~7;
+  }
 }
 
 template <typename T>
@@ -418,7 +433,8 @@ __global__ void __launch_bounds__(PLAN_THREADS) task_bounds_kernel(const double*
 long long scan_partials_needed(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, const double* d_P, double* d_C,
-                            double* d_partials, long long* d_task_start, int T, cudaStream_t s) {
+                            double* d_partials, long long* d_task_start, int T, int* d_slot32, int tiny_slots,
+                            cudaStream_t s) {
   if (n_items <= 0) {
     // empty plan: a single empty task
     long long z[2] = {0, 0};
@@ -426,7 +442,7 @@ void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, 
     return;
   }
   unsigned nb = (unsigned)((n_items + PLAN_THREADS - 1) / PLAN_THREADS);
-  costs_kernel<<<nb, PLAN_THREADS, 0, s>>>(d_graphs, G, n_items, d_P, d_C);
+  costs_kernel<<<nb, PLAN_THREADS, 0, s>>>(d_graphs, G, n_items, d_P, d_C, d_slot32, tiny_slots);
   long long nt = (n_items + SCAN_TILE - 1) / SCAN_TILE;
   tile_reduce_kernel<double><<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
   partials_scan_kernel<double><<<1, 1024, 0, s>>>(d_partials, nt, nullptr);

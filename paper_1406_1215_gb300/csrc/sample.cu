@@ -1,5 +1,5 @@
-// sample.cu -- the count and emit passes: Algorithm 1 (Create-Edges) run per
-// item by one lane each.
+// sample.cu -- the sampling passes: Algorithm 1 (Create-Edges) run per item
+// by one lane each, and the copy of staged destinations into the edge list.
 //
 // Scheduling (Section 4 analogue): a persistent grid; each warp pulls the
 // next equal-cost task (Eq. 3) from a counter; inside the warp every lane
@@ -15,6 +15,19 @@
 //   stop if delta >= end - j;  v = j + delta
 //   Q_v = min(w_u w_v, S); accept iff r_a Q_prev < Q_v (exact, 128-bit)
 //   Q_prev = Q_v (recompute L_p if it changed); j = v + 1
+// A new item's first position is handled by the same weight-lookup and
+// L_p stages as a candidate (Q_prev = Q(j0)), so set-up shares the code of
+// the loop body instead of running as a separate divergent branch.
+//
+// Modes: COUNT writes per-item edge counts; STAGE also writes each item's
+// destinations, in order, into the item's slot of a staging pool (slot sizes
+// come from the plan: expected edges + 4 sd + 8, in whole 32-byte sectors;
+// an item that outgrows its slot is regenerated by EMIT).  A lane collects 8
+// entries in shared memory and writes them as one whole sector, since a
+// partially written sector costs a read-modify-write of HBM when evicted;
+// EMIT regenerates items and writes (u, v) pairs.  The copy kernel turns
+// staged destinations into (u, v) pairs at the scanned offsets, so a count
+// + copy does the sampling arithmetic once.
 #include <cuda_runtime.h>
 
 #include "cl_internal.cuh"
@@ -24,6 +37,9 @@
 namespace cl {
 
 constexpr int SAMPLER_THREADS = 256;
+constexpr unsigned GROUP = 8;  // entries per staged write: one 32-byte sector
+
+enum { MODE_COUNT = 0, MODE_STAGE = 1, MODE_EMIT = 2 };
 
 __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
 
@@ -35,15 +51,20 @@ __device__ __forceinline__ bool accept_i(unsigned long long k, unsigned long lon
   return hi < rhi || (hi == rhi && lo < rlo);
 }
 
-template <bool EMIT, typename E>
-__global__ void __launch_bounds__(SAMPLER_THREADS) sample_kernel(DevPlan P, long long ib, long long ie,
-                                                                 const long long* __restrict__ offsets,
-                                                                 E* __restrict__ edges, long long capacity,
-                                                                 int* __restrict__ counts) {
+// Software pipelining: a lane issues the load of its candidate's weight and,
+// while it is in flight, computes the Philox block and -ln r_s of its next
+// draw; the candidate is then accepted or rejected with the draw it was made
+// with.  Single-graph plans read the graph's parameters from the kernel
+// parameter (constant bank) instead of per-lane registers.
+template <int MODE, bool SINGLE, typename E>
+__global__ void __launch_bounds__(SAMPLER_THREADS, 4)
+    sample_kernel(DevPlan P, DevGraph G1, long long ib, long long ie, const long long* __restrict__ offsets,
+                  E* __restrict__ edges, long long capacity, int* __restrict__ counts, int regen_only) {
   const int lane = threadIdx.x & 31;
   const unsigned lanemask_lt = (1u << lane) - 1u;
   long long off_base = 0;
-  if (EMIT) {
+  if (MODE == MODE_EMIT) {
+    if (regen_only && *(volatile int*)P.overflow == 0) return;  // every item fit in its slot
     off_base = offsets[ib];
     if (offsets[ie] - off_base > capacity) {
       if (blockIdx.x == 0 && threadIdx.x == 0) set_error(P.err, CL_ERR_CAPACITY);
@@ -54,17 +75,26 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sample_kernel(DevPlan P, long
   long long next = 0, tend = 0;
   bool tasks_left = true;
   // lane state
-  bool have = false;
+  bool have = false, fresh = false;
   long long item = 0, obase = 0;
-  const int* w = nullptr;
-  unsigned u = 0, seg = 0, j = 0, end = 0, t = 0, k = 0, key0 = 0, key1 = 0;
-  unsigned long long S = 0, Qprev = 0;
-  int wu = 0;
+  unsigned u = 0, seg = 0, j = 0, end = 0, t = 0, k = 0;
+  unsigned long long Qprev = 0;
   ff Lp{0.f, 0.f};
+  int wu = 0;
+  u32x4 pb{0u, 0u, 0u, 0u};  // the lane's next draw (index t) ...
+  ff pLr{0.f, 0.f};          // ... and its -ln r_s
+  // graph of the lane's item (batched plans only)
+  const int* w_l = nullptr;
+  unsigned long long S_l = 0;
+  float Sh_l = 0.f, Sl_l = 0.f;
+  unsigned k0_l = 0, k1_l = 0;
+  unsigned long long sbase = 0;  // staging: the item's slot and its size
+  unsigned ssize = 0;
+  __shared__ unsigned sgrp[MODE == MODE_STAGE ? GROUP : 1][SAMPLER_THREADS];  // staging group, [entry][thread]
   unsigned long long n_iter = 0, n_fb = 0, n_tie = 0;
 
   while (true) {
-    // ---- refill lanes that have no item
+    // ---- (1) lanes without an item take the next items of the warp's task
     unsigned need = __ballot_sync(FULL_MASK, !have);
     while (need) {
       if (next >= tend) {
@@ -86,97 +116,141 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sample_kernel(DevPlan P, long
       int taken = __popc(need);
       if (!have && rank < avail) {
         item = next + rank;
-        // ---- item set-up
-        int gi = P.G == 1 ? 0 : graph_of_item(P.graphs, P.G, item);
-        const DevGraph& g = P.graphs[gi];
-        unsigned j0;
-        item_bounds(g, item - g.item_begin, u, seg, j0, end);
-        w = (const int*)g.w;
-        S = (unsigned long long)g.S_i;
-        key0 = g.key0;
-        key1 = g.key1;
-        wu = __ldg(&w[u]);
-        j = j0;
-        t = 0;
-        k = 0;
-        unsigned long long q = (unsigned long long)((long long)wu * (long long)__ldg(&w[j0]));
-        Qprev = q < S ? q : S;
-        if (EMIT) obase = offsets[item] - off_base;
-        if (Qprev == 0 || j0 >= end) {
-          if (!EMIT) counts[item] = 0;  // empty item: no draw at all
-        } else {
-          have = true;
-          if (Qprev < S) Lp = ff_neglog_ratio(S - Qprev, S);
-        }
+        have = true;
+        fresh = true;
+        if (MODE == MODE_EMIT && regen_only &&
+            offsets[item + 1] - offsets[item] <= P.slot_base[item + 1] - P.slot_base[item])
+          have = fresh = false;  // staged: the copy kernel wrote it
       }
       next += taken < avail ? taken : avail;
-      need = __ballot_sync(FULL_MASK, !have);  // empty items and unserved lanes retry at once
+      need = __ballot_sync(FULL_MASK, !have);
     }
     if (!__any_sync(FULL_MASK, have)) {
       if (!tasks_left) break;
       continue;
     }
-    // ---- one iteration of the skip loop
-    if (have) {
-      u32x4 b = philox4x32_10(u32x4{t, seg, u, 0u}, key0, key1);
+
+    unsigned target = 0;
+    bool look = false, done = false;
+    // ---- (2) set-up of new items: bounds, graph, w_u
+    if (have && fresh) {
+      unsigned j0;
+      if (SINGLE) {
+        item_bounds(G1, item, u, seg, j0, end);
+      } else {
+        int gi = graph_of_item(P.graphs, P.G, item);
+        const DevGraph& g = P.graphs[gi];
+        item_bounds(g, item - g.item_begin, u, seg, j0, end);
+        w_l = (const int*)g.w;
+        S_l = (unsigned long long)g.S_i;
+        Sh_l = g.S_ff_hi;
+        Sl_l = g.S_ff_lo;
+        k0_l = g.key0;
+        k1_l = g.key1;
+      }
+      wu = __ldg(&(SINGLE ? (const int*)G1.w : w_l)[u]);
+      t = 0;
+      k = 0;
+      if (MODE == MODE_EMIT) obase = offsets[item] - off_base;
+      if (MODE == MODE_STAGE) {
+        sbase = P.slot_base[item];
+        ssize = (unsigned)(P.slot_base[item + 1] - sbase);
+      }
+      target = j0;  // first position: p = Q(j0) / S
+      look = true;
+    }
+    const int* W = SINGLE ? (const int*)G1.w : w_l;
+    const unsigned long long S = SINGLE ? (unsigned long long)G1.S_i : S_l;
+    // ---- (3) one skip for running items, with the precomputed draw t
+    const u32x4 cur = pb;
+    if (have && !fresh) {
       ++t;
       ++n_iter;
       long long R = (long long)end - (long long)j;
       long long delta = 0;
       if (Qprev != S) {
-        unsigned long long Ar = 2ull * grid52(b.x, b.y) + 1ull;
-        ff Lr = ff_neglog_ratio(Ar, 1ull << 53);
-        delta = floor_decide_ff(ff_div(Lr, Lp), R);
+        delta = floor_decide_ff(ff_div(pLr, Lp), R);
         if (delta == SKIP_UNDECIDED) {
           bool tie;
-          delta = skip_fallback_dd(Ar, S - Qprev, S, R, &tie);
+          delta = skip_fallback_dd(2ull * grid52(cur.x, cur.y) + 1ull, S - Qprev, S, R, &tie);
           ++n_fb;
           n_tie += tie;
         }
       }
-      bool done = false;
       if (delta >= R) {
-        done = true;
+        done = true;  // the candidate falls past the end of the item
       } else {
-        unsigned v = j + (unsigned)delta;
-        int wv = __ldg(&w[v]);
-        unsigned long long q = (unsigned long long)((long long)wu * (long long)wv);
-        unsigned long long Qv = q < S ? q : S;
-        bool acc = (Qv == Qprev) || accept_i(grid52(b.z, b.w), Qprev, Qv);
+        target = j + (unsigned)delta;
+        look = true;
+      }
+    }
+    if (look) {
+      // ---- (4) weight of the candidate (or of the first position); meanwhile the next draw
+      const int wt = __ldg(&W[target]);
+      pb = philox4x32_10(u32x4{t, seg, u, 0u}, SINGLE ? G1.key0 : k0_l, SINGLE ? G1.key1 : k1_l);
+      pLr = ff_neglog_r53(2ull * grid52(pb.x, pb.y) + 1ull);
+      unsigned long long q = (unsigned long long)((long long)wu * (long long)wt);
+      const unsigned long long Qt = q < S ? q : S;
+      // ---- (5) acceptance r_a < q / p, with the draw that made the candidate
+      if (!fresh) {
+        bool acc = (Qt == Qprev) || accept_i(grid52(cur.z, cur.w), Qprev, Qt);
         if (acc) {
-          if (EMIT) {
+          if (MODE == MODE_EMIT) {
             long long pos = obase + k;
             if (pos < capacity) {
               E e;
               e.x = u;
-              e.y = v;
+              e.y = target;
               edges[pos] = e;
+            }
+          }
+          if (MODE == MODE_STAGE) {
+            if (k < ssize) {
+              unsigned e8 = k & (GROUP - 1);
+              sgrp[e8][threadIdx.x] = target;
+              if (e8 == GROUP - 1) {
+                uint4* dst = (uint4*)(P.pool + sbase + (k & ~(GROUP - 1)));
+                dst[0] = make_uint4(sgrp[0][threadIdx.x], sgrp[1][threadIdx.x], sgrp[2][threadIdx.x],
+                                    sgrp[3][threadIdx.x]);
+                dst[1] = make_uint4(sgrp[4][threadIdx.x], sgrp[5][threadIdx.x], sgrp[6][threadIdx.x],
+                                    sgrp[7][threadIdx.x]);
+              }
+            } else if (k == ssize) {
+              atomicExch(P.overflow, 1);  // the item outgrew its slot: EMIT regenerates it
             }
           }
           ++k;
         }
-        if (Qv != Qprev) {
-          Qprev = Qv;
-          if (Qv == 0)
-            done = true;
-          else if (Qv < S)
-            Lp = ff_neglog_ratio(S - Qv, S);
-        }
-        j = v + 1;
-        if (j >= end) done = true;
       }
-      if (done) {
-        if (EMIT) {
-          long long expect = offsets[item + 1] - offsets[item];
-          if ((long long)k != expect) set_error(P.err, CL_ERR_DEVICE);
-        } else {
-          counts[item] = (int)k;
-        }
-        have = false;
+      // ---- (6) p <- q: a new L_p when q changed (and for a new item)
+      if (fresh || Qt != Qprev) {
+        Qprev = Qt;
+        if (Qt == 0)
+          done = true;  // p = 0: no further edge
+        else if (Qt < S)
+          Lp = ff_neglog1m(Qt, S, SINGLE ? ff{G1.S_ff_hi, G1.S_ff_lo} : ff{Sh_l, Sl_l});
       }
+      j = fresh ? target : target + 1;
+      if (j >= end) done = true;
+      fresh = false;
+    }
+    // ---- (7) item end
+    if (have && done) {
+      if (MODE == MODE_EMIT) {
+        long long expect = offsets[item + 1] - offsets[item];
+        if ((long long)k != expect) set_error(P.err, CL_ERR_DEVICE);
+      } else {
+        counts[item] = (int)k;
+        if (MODE == MODE_STAGE && k <= ssize) {  // the item's last partial group
+          unsigned c = k & (GROUP - 1);
+          unsigned long long base = sbase + (k & ~(GROUP - 1));
+          for (unsigned i = 0; i < c; ++i) P.pool[base + i] = sgrp[i][threadIdx.x];
+        }
+      }
+      have = false;
     }
   }
-  if (!EMIT) {
+  if (MODE != MODE_EMIT) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       n_iter += __shfl_xor_sync(FULL_MASK, n_iter, o);
@@ -191,30 +265,151 @@ __global__ void __launch_bounds__(SAMPLER_THREADS) sample_kernel(DevPlan P, long
   }
 }
 
+// ---- copy of staged destinations.  A warp takes 32 consecutive items; their
+// edges form one contiguous output range, which the lanes cover edge by edge
+// (consecutive lanes write consecutive pairs); each lane finds its edge's item
+// by a 5-step search over the warp's inclusive count prefix, so every load is
+// independent of the others.
+constexpr int COPY_THREADS = 256;
+
+template <typename E>
+__global__ void __launch_bounds__(COPY_THREADS) copy_kernel(DevPlan P, long long ib, long long ie,
+                                                            const long long* __restrict__ offsets,
+                                                            E* __restrict__ edges, long long capacity) {
+  const int lane = threadIdx.x & 31;
+  const long long off_base = offsets[ib];
+  if (offsets[ie] - off_base > capacity) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_error(P.err, CL_ERR_CAPACITY);
+    return;
+  }
+  while (true) {
+    unsigned c = 0;
+    if (lane == 0) c = atomicAdd(P.task_ctr, 1u);
+    c = __shfl_sync(FULL_MASK, c, 0);
+    long long i0 = ib + (long long)c * 32;
+    if (i0 >= ie) break;
+    long long i = i0 + lane;
+    long long o = 0, pos = 0;
+    int cnt = 0;
+    unsigned uu = 0;
+    if (i < ie) {
+      o = offsets[i] - off_base;
+      long long cc = offsets[i + 1] - offsets[i];
+      pos = P.slot_base[i];
+      if (cc <= P.slot_base[i + 1] - pos) cnt = (int)cc;  // else: not staged, regenerated
+      if (cnt > 0) {
+        int gi = P.G == 1 ? 0 : graph_of_item(P.graphs, P.G, i);
+        const DevGraph& g = P.graphs[gi];
+        unsigned sg, j0, en;
+        item_bounds(g, i - g.item_begin, uu, sg, j0, en);
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int y = __shfl_up_sync(FULL_MASK, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(FULL_MASK, incl, 31);
+    constexpr int U = 4;  // edges per lane per step: independent loads in flight
+    for (int base = 0; base < total; base += 32 * U) {
+      long long dst[U];
+      unsigned src_u[U];
+      unsigned val[U];
+      bool ok[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        int e = base + 32 * q + lane;
+        // smallest lane l with incl_l > e (it has cnt_l > 0)
+        int lo = 0, hi = 31;
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          int mid = (lo + hi) >> 1;
+          int iv = __shfl_sync(FULL_MASK, incl, mid);
+          if (iv > e)
+            hi = mid;
+          else
+            lo = mid + 1;
+        }
+        int il = __shfl_sync(FULL_MASK, incl, lo);
+        int cl = __shfl_sync(FULL_MASK, cnt, lo);
+        long long ol = __shfl_sync(FULL_MASK, o, lo);
+        long long pl = __shfl_sync(FULL_MASK, pos, lo);
+        src_u[q] = __shfl_sync(FULL_MASK, uu, lo);
+        ok[q] = e < total;
+        int local = e - (il - cl);
+        dst[q] = ol + local;
+        val[q] = ok[q] ? P.pool[pl + local] : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (ok[q]) {
+          E pr;
+          pr.x = src_u[q];
+          pr.y = val[q];
+          edges[dst[q]] = pr;
+        }
+      }
+    }
+  }
+}
+
 int sampler_max_blocks_per_sm(int block, bool emit, int etype) {
   int nb = 0;
   if (!emit)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<false, int2>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_STAGE, false, int2>, block, 0);
   else if (etype == CL_E_I32)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<true, int2>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_EMIT, false, int2>, block, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<true, longlong2>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_EMIT, false, longlong2>, block, 0);
   return nb;
 }
 
-void launch_count(const DevPlan& P, int* d_counts, int block, int grid, cudaStream_t s) {
-  cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
-  sample_kernel<false, int2><<<grid, block, 0, s>>>(P, 0, P.n_items, nullptr, nullptr, 0, d_counts);
+template <int MODE, typename E>
+static void launch_sampler(const DevPlan& P, const DevGraph* single, long long ib, long long ie,
+                           const long long* offsets, E* edges, long long capacity, int* counts, int regen, int block,
+                           int grid, cudaStream_t s) {
+  if (single)
+    sample_kernel<MODE, true, E>
+        <<<grid, block, 0, s>>>(P, *single, ib, ie, offsets, edges, capacity, counts, regen);
+  else
+    sample_kernel<MODE, false, E>
+        <<<grid, block, 0, s>>>(P, DevGraph{}, ib, ie, offsets, edges, capacity, counts, regen);
 }
 
-void launch_emit(const DevPlan& P, const long long* d_offsets, long long ib, long long ie, int etype, void* d_edges,
-                 long long capacity, int block, int grid, cudaStream_t s) {
+void launch_count(const DevPlan& P, const DevGraph* single, int* d_counts, bool stage, int block, int grid,
+                  cudaStream_t s) {
   cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
+  if (stage) {
+    cudaMemsetAsync(P.overflow, 0, sizeof(int), s);
+    launch_sampler<MODE_STAGE, int2>(P, single, 0, P.n_items, nullptr, nullptr, 0, d_counts, 0, block, grid, s);
+  } else {
+    launch_sampler<MODE_COUNT, int2>(P, single, 0, P.n_items, nullptr, nullptr, 0, d_counts, 0, block, grid, s);
+  }
+}
+
+void launch_emit(const DevPlan& P, const DevGraph* single, const long long* d_offsets, long long ib, long long ie,
+                 int etype, void* d_edges, long long capacity, bool staged, int block, int grid, cudaStream_t s) {
+  cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
+  if (staged) {
+    long long chunks = (ie - ib + 31) / 32;
+    long long cg = (chunks + 7) / 8;
+    int cgrid = (int)(cg < 4096 ? (cg < 1 ? 1 : cg) : 4096);
+    if (etype == CL_E_I32)
+      copy_kernel<int2><<<cgrid, COPY_THREADS, 0, s>>>(P, ib, ie, d_offsets, (int2*)d_edges, capacity);
+    else
+      copy_kernel<longlong2><<<cgrid, COPY_THREADS, 0, s>>>(P, ib, ie, d_offsets, (longlong2*)d_edges, capacity);
+    // items that outgrew their slots are regenerated (the kernel returns at
+    // once when none did)
+    cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
+  }
+  int regen = staged ? 1 : 0;
   if (etype == CL_E_I32)
-    sample_kernel<true, int2><<<grid, block, 0, s>>>(P, ib, ie, d_offsets, (int2*)d_edges, capacity, nullptr);
+    launch_sampler<MODE_EMIT, int2>(P, single, ib, ie, d_offsets, (int2*)d_edges, capacity, nullptr, regen, block,
+                                    grid, s);
   else
-    sample_kernel<true, longlong2>
-        <<<grid, block, 0, s>>>(P, ib, ie, d_offsets, (longlong2*)d_edges, capacity, nullptr);
+    launch_sampler<MODE_EMIT, longlong2>(P, single, ib, ie, d_offsets, (longlong2*)d_edges, capacity, nullptr,
+                                         regen, block, grid, s);
 }
 
 // Per-graph edge offsets of a batch and the capacity status.
