@@ -37,9 +37,9 @@ struct cl_plan {
   size_t ws_bytes = 0;
   DevGraph* d_graphs = nullptr;
   long long* d_tile_begin = nullptr;
-  double* d_P = nullptr;
-  double* d_C = nullptr;
-  double* d_part = nullptr;
+  void* d_P = nullptr;
+  long long* d_C = nullptr;
+  long long* d_part = nullptr;
   long long* d_scan_part = nullptr;
   long long* d_task = nullptr;
   unsigned* d_ctr = nullptr;
@@ -49,7 +49,13 @@ struct cl_plan {
   int* d_slot32 = nullptr;
   long long* d_slot_base = nullptr;
   int* d_overflow = nullptr;
+  long long* d_ovf_list = nullptr;
+  unsigned* d_ovf_count = nullptr;
 };
+
+namespace {
+constexpr unsigned OVF_CAP = 1u << 20;  // items listed for regeneration (beyond: scan all items)
+}
 
 namespace {
 
@@ -102,9 +108,9 @@ ScratchLayout scratch_layout(void* base, int G, bool f64) {
 struct WsLayout {
   DevGraph* graphs;
   long long* tile_begin;
-  double* P;
-  double* C;
-  double* part;
+  void* P;
+  long long* C;
+  long long* part;
   long long* scan_part;
   long long* task;
   unsigned* ctr;
@@ -113,6 +119,8 @@ struct WsLayout {
   int* overflow;
   int* slot32;
   long long* slot_base;
+  long long* ovf_list;
+  unsigned* ovf_count;
   unsigned* pool;
   size_t bytes;
 };
@@ -124,9 +132,9 @@ WsLayout ws_layout(void* base, const cl_plan* p) {
   long long nt = (p->ntiles > nt_items ? p->ntiles : nt_items) + 1;
   L.graphs = c.take<DevGraph>(p->G);
   L.tile_begin = c.take<long long>(p->G + 1);
-  L.P = c.take<double>(p->psize > 0 ? p->psize : 1);
-  L.C = c.take<double>(p->n_items > 0 ? p->n_items : 1);
-  L.part = c.take<double>(nt + (nt + 7) / 8);  // partials + one head byte per tile
+  L.P = c.take<long long>(p->psize > 0 ? p->psize : 1);  // int64 or double prefix
+  L.C = c.take<long long>(p->n_items > 0 ? p->n_items : 1);
+  L.part = c.take<long long>(nt);
   L.scan_part = c.take<long long>(nt_items + 1);
   L.task = c.take<long long>(p->T + 1);
   L.ctr = c.take<unsigned>(4);
@@ -135,6 +143,8 @@ WsLayout ws_layout(void* base, const cl_plan* p) {
   L.overflow = c.take<int>(4);
   L.slot32 = p->stage ? c.take<int>(p->n_items > 0 ? p->n_items : 1) : nullptr;
   L.slot_base = p->stage ? c.take<long long>(p->n_items + 1) : nullptr;
+  L.ovf_list = p->stage ? c.take<long long>(OVF_CAP) : nullptr;
+  L.ovf_count = c.take<unsigned>(4);
   L.pool = p->stage ? c.take<unsigned>(p->pool_cap > 0 ? p->pool_cap : 1) : nullptr;
   L.bytes = c.off;
   return L;
@@ -153,6 +163,9 @@ DevPlan dev_plan(const cl_plan* p) {
   P.pool = p->d_pool;
   P.slot_base = p->d_slot_base;
   P.overflow = p->d_overflow;
+  P.ovf_list = p->d_ovf_list;
+  P.ovf_count = p->d_ovf_count;
+  P.ovf_cap = OVF_CAP;
   return P;
 }
 
@@ -273,6 +286,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
       d.S_ff_lo = (float)(d.S_i - (long long)hi);
       if (gs == CL_OK && res[g].S_i >= (1ull << 53)) gs = CL_ERR_RANGE;
     }
+    d.invS_f = d.S_d > 0 ? (float)(1.0 / d.S_d) : 0.0f;
     d.H = (long long)res[g].H;
     d.Hh = d.H < n - 1 ? d.H : (n > 0 ? n - 1 : 0);
     d.n_heavy = d.Hh > 0 ? heavy_items_before(d.Hh, n) : 0;
@@ -371,6 +385,8 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   p->d_slot32 = L.slot32;
   p->d_slot_base = L.slot_base;
   p->d_overflow = L.overflow;
+  p->d_ovf_list = L.ovf_list;
+  p->d_ovf_count = L.ovf_count;
   cl_status st;
   if ((st = cuda_ok(cudaMemcpyAsync(L.graphs, p->dg.data(), sizeof(DevGraph) * p->G, cudaMemcpyHostToDevice, s))))
     return st;
@@ -381,9 +397,11 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   if ((st = cuda_ok(cudaMemsetAsync(L.err, 0, 4 * sizeof(int), s)))) return st;
   if ((st = cuda_ok(cudaMemsetAsync(L.stats, 0, 4 * sizeof(unsigned long long), s)))) return st;
   if ((st = cuda_ok(cudaMemsetAsync(L.overflow, 0, 4 * sizeof(int), s)))) return st;
-  launch_weight_prefix(L.graphs, L.tile_begin, p->G, p->ntiles, L.P, L.part, s);
-  launch_costs_and_tasks(L.graphs, p->G, p->n_items, L.P, L.C, L.part, L.task, p->T, L.slot32, p->tiny_slots ? 1 : 0,
-                         s);
+  if ((st = cuda_ok(cudaMemsetAsync(L.ovf_count, 0, 4 * sizeof(unsigned), s)))) return st;
+  const bool f64 = p->wtype == CL_W_F64;
+  launch_weight_prefix(L.graphs, L.tile_begin, p->G, p->ntiles, f64, L.P, L.part, s);
+  launch_costs_and_tasks(L.graphs, p->G, p->n_items, f64, L.P, L.C, L.part, L.task, p->T, L.slot32,
+                         p->tiny_slots ? 1 : 0, s);
   if (p->stage) launch_count_scan(L.slot32, p->n_items, L.slot_base, L.scan_part, s);  // slot bases
   if ((st = last_ok())) return st;
   p->built = true;

@@ -27,7 +27,7 @@ struct DevGraph {
   long long pbase;        // offset of this graph's weight prefix (n + 1 entries)
   int wtype;              // cl_wtype
   float S_ff_hi, S_ff_lo; // S as float-float (integer weights)
-  int pad_;
+  float invS_f;           // 1 / S in single precision (costs only)
 };
 
 // Per-graph results of the analysis kernel (scratch of cl_plan_create).
@@ -102,6 +102,9 @@ struct DevPlan {
   unsigned* pool;               // staging pool of destination nodes
   const long long* slot_base;   // per item: first pool entry of its slot (n_items + 1 entries)
   int* overflow;                // set when an item outgrew its slot
+  long long* ovf_list;          // items that outgrew their slot (first ovf_cap of them)
+  unsigned* ovf_count;
+  unsigned ovf_cap;
 };
 
 // ---- launchers implemented in plan.cu / sample.cu / diag.cu ----
@@ -113,14 +116,15 @@ void launch_analyze(const DevGraph* d_graphs, const long long* d_blk_begin, int 
 void launch_f64_sum_finalize(int G, const unsigned long long* d_bins, GraphAnalysis* d_out, cudaStream_t s);
 size_t f64_bins_bytes(int G);
 
-// Weight prefix P_g[u] = sum_{v<u} w_v for u = 0..n_g (as double), tile-segmented by graph.
+// Weight prefix over the graphs' concatenated weights (int64 for integer weights, double
+// for double weights); graph g's entries start at pbase_g.
 void launch_weight_prefix(const DevGraph* d_graphs, const long long* d_tile_graph_begin, int G, long long ntiles,
-                          double* d_P, double* d_partials, cudaStream_t s);
-// Item costs c_i, inclusive prefix C in place, task boundaries (Eq. 3); when d_slot32
-// is given, also the staging slot sizes (8-aligned, int32) of every item.
-void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, const double* d_P, double* d_C,
-                            double* d_partials, long long* d_task_start, int T, int* d_slot32, int tiny_slots,
-                            cudaStream_t s);
+                          bool f64, void* d_P, void* d_partials, cudaStream_t s);
+// Item costs (fixed point, 1/16 edge), their exact inclusive prefix C in place and the
+// task boundaries of Eq. 3; when d_slot32 is given, also every item's staging slot size.
+void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, bool f64, const void* d_P,
+                            long long* d_C, long long* d_partials, long long* d_task_start, int T, int* d_slot32,
+                            int tiny_slots, cudaStream_t s);
 // Exclusive int32 -> int64 scan with the total at out[n].
 void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, long long* d_partials,
                        cudaStream_t s);

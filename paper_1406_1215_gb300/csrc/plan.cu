@@ -287,53 +287,52 @@ void launch_f64_sum_finalize(int G, const unsigned long long* d_bins, GraphAnaly
 }
 
 // --------------------------------------------------------------- weight prefix
-__device__ __forceinline__ double weight_at(const DevGraph& g, long long u) {
-  if (u >= g.n) return 0.0;
-  if (g.wtype == CL_W_F64) return ((const double*)g.w)[u];
-  return (double)((const int*)g.w)[u];
+// sigma over the concatenation of the graphs' weight arrays, each followed by
+// one zero (so graph g's prefix P[pbase_g + u], u = 0..n_g, differs from
+// sigma_u by the constant P[pbase_g], which cancels in every difference the
+// costs use).  Exact int64 for integer weights; double for double weights.
+template <typename T>
+__device__ __forceinline__ T weight_at(const DevGraph& g, long long u) {
+  if (u >= g.n) return T(0);
+  if (g.wtype == CL_W_F64) return (T)((const double*)g.w)[u];
+  return (T)((const int*)g.w)[u];
 }
 
+template <typename T>
 __global__ void __launch_bounds__(PLAN_THREADS) wprefix_reduce_kernel(const DevGraph* __restrict__ gs,
                                                                       const long long* __restrict__ tbeg, int G,
-                                                                      double* __restrict__ part,
-                                                                      unsigned char* __restrict__ head) {
+                                                                      T* __restrict__ part) {
   const long long t = blockIdx.x;
   const int g = block_graph(tbeg, G, t);
   const DevGraph& gr = gs[g];
-  const long long lt = t - tbeg[g];
-  const long long e0 = lt * SCAN_TILE, len = gr.n + 1;
-  double acc = 0.0;
+  const long long e0 = (t - tbeg[g]) * SCAN_TILE, len = gr.n + 1;
+  T acc = T(0);
   for (int k = 0; k < SCAN_ITEMS; ++k) {
     long long u = e0 + (long long)k * PLAN_THREADS + threadIdx.x;
-    if (u < len) acc += weight_at(gr, u);
+    if (u < len) acc += weight_at<T>(gr, u);
   }
-  double tot = block_reduce(acc);
-  if (threadIdx.x == 0) {
-    part[t] = tot;
-    head[t] = lt == 0;
-  }
+  T tot = block_reduce(acc);
+  if (threadIdx.x == 0) part[t] = tot;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(PLAN_THREADS) wprefix_scan_kernel(const DevGraph* __restrict__ gs,
                                                                     const long long* __restrict__ tbeg, int G,
-                                                                    const double* __restrict__ part,
-                                                                    double* __restrict__ P) {
+                                                                    const T* __restrict__ part, T* __restrict__ P) {
   const long long t = blockIdx.x;
   const int g = block_graph(tbeg, G, t);
   const DevGraph& gr = gs[g];
-  const long long lt = t - tbeg[g];
-  const long long e0 = lt * SCAN_TILE, len = gr.n + 1;
-  // each thread owns SCAN_ITEMS consecutive elements
+  const long long e0 = (t - tbeg[g]) * SCAN_TILE, len = gr.n + 1;
   long long u0 = e0 + (long long)threadIdx.x * SCAN_ITEMS;
-  double v[SCAN_ITEMS];
-  double loc = 0.0;
+  T v[SCAN_ITEMS];
+  T loc = T(0);
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    v[k] = (u0 + k < len) ? weight_at(gr, u0 + k) : 0.0;
+    v[k] = (u0 + k < len) ? weight_at<T>(gr, u0 + k) : T(0);
     loc += v[k];
   }
-  double tot;
-  double ex = block_excl_scan(loc, &tot) + part[t];
+  T tot;
+  T ex = block_excl_scan(loc, &tot) + part[t];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
     if (u0 + k < len) P[gr.pbase + u0 + k] = ex;
@@ -342,20 +341,33 @@ __global__ void __launch_bounds__(PLAN_THREADS) wprefix_scan_kernel(const DevGra
 }
 
 void launch_weight_prefix(const DevGraph* d_graphs, const long long* d_tile_graph_begin, int G, long long ntiles,
-                          double* d_P, double* d_partials, cudaStream_t s) {
+                          bool f64, void* d_P, void* d_partials, cudaStream_t s) {
   if (ntiles <= 0) return;
-  unsigned char* head = (unsigned char*)(d_partials + ntiles);
-  wprefix_reduce_kernel<<<(unsigned)ntiles, PLAN_THREADS, 0, s>>>(d_graphs, d_tile_graph_begin, G, d_partials, head);
-  partials_scan_kernel<double><<<1, 1024, 0, s>>>(d_partials, ntiles, head);
-  wprefix_scan_kernel<<<(unsigned)ntiles, PLAN_THREADS, 0, s>>>(d_graphs, d_tile_graph_begin, G, d_partials, d_P);
+  if (f64) {
+    wprefix_reduce_kernel<double><<<(unsigned)ntiles, PLAN_THREADS, 0, s>>>(d_graphs, d_tile_graph_begin, G,
+                                                                           (double*)d_partials);
+    partials_scan_kernel<double><<<1, 1024, 0, s>>>((double*)d_partials, ntiles, nullptr);
+    wprefix_scan_kernel<double><<<(unsigned)ntiles, PLAN_THREADS, 0, s>>>(
+        d_graphs, d_tile_graph_begin, G, (const double*)d_partials, (double*)d_P);
+  } else {
+    wprefix_reduce_kernel<long long><<<(unsigned)ntiles, PLAN_THREADS, 0, s>>>(d_graphs, d_tile_graph_begin, G,
+                                                                              (long long*)d_partials);
+    partials_scan_kernel<long long><<<1, 1024, 0, s>>>((long long*)d_partials, ntiles, nullptr);
+    wprefix_scan_kernel<long long><<<(unsigned)ntiles, PLAN_THREADS, 0, s>>>(
+        d_graphs, d_tile_graph_begin, G, (const long long*)d_partials, (long long*)d_P);
+  }
 }
 
 // --------------------------------------------------------------- costs, Eq. 3
 // c_i = 1 + (w_u / S) * sum_{v in [j0, end)} w_v  (Eq. 1-2; for a light row
-// [u+1, n) this is Eq. 6: (w_u / S)(S - sigma_u - w_u) + 1).
+// [u+1, n) this is Eq. 6: (w_u / S)(S - sigma_u - w_u) + 1), in fixed point
+// with 1/16-edge units so that its prefix is an exact integer.  Costs only
+// schedule work, so single precision is enough for their value (FP64 runs at
+// 1/75 of FP32 here).
+template <typename T>
 __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __restrict__ gs, int G,
-                                                             long long n_items, const double* __restrict__ P,
-                                                             double* __restrict__ C, int* __restrict__ slot,
+                                                             long long n_items, const T* __restrict__ P,
+                                                             long long* __restrict__ C, int* __restrict__ slot,
                                                              int tiny_slots) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n_items) return;
@@ -363,47 +375,46 @@ __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __r
   const DevGraph& gr = gs[g];
   unsigned u, seg, j0, end;
   item_bounds(gr, i - gr.item_begin, u, seg, j0, end);
-  double wu = weight_at(gr, u);
-  const double* Pg = P + gr.pbase;
-  double S = gr.S_d > 0 ? gr.S_d : 1.0;
-  double e = wu / S * (Pg[end] - Pg[j0]);  // expected edges of the item (uncapped)
-  C[i] = 1.0 + e;
+  float wu = (float)weight_at<T>(gr, u);
+  float dP = (float)(P[gr.pbase + end] - P[gr.pbase + j0]);
+  float e = wu * dP * gr.invS_f;  // expected edges of the item (uncapped)
+  e = fminf(e, 1e15f);
+  C[i] = 16ll + (long long)(16.0f * e + 0.5f);
   if (slot) {
     // staging slot: e + 4 sd + 8 entries in whole sectors, at most the item's length
-    double want = tiny_slots ? 8.0 : e + 4.0 * sqrt(e) + 8.0;
-    double len = (double)(end - j0);
-    if (want > len) want = len;
-    if (want > 1e9) want = 1e9;
-    slot[i] = ((int)ceil(want) + 7) & ~7;
+    float want = tiny_slots ? 8.0f : e + 4.0f * sqrtf(e) + 8.0f;
+    float len = (float)(end - j0);
+    want = fminf(want, len);
+    want = fminf(want, 1e9f);
+    slot[i] = ((int)ceilf(want) + 7) & ~7;
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PLAN_THREADS) tile_reduce_kernel(const T* __restrict__ x, long long n,
-                                                                   T* __restrict__ part) {
+__global__ void __launch_bounds__(PLAN_THREADS) tile_reduce_i64_kernel(const long long* __restrict__ x, long long n,
+                                                                       long long* __restrict__ part) {
   long long e0 = blockIdx.x * (long long)SCAN_TILE;
-  T acc = T(0);
+  long long acc = 0;
   for (int k = 0; k < SCAN_ITEMS; ++k) {
     long long i = e0 + (long long)k * PLAN_THREADS + threadIdx.x;
     if (i < n) acc += x[i];
   }
-  T tot = block_reduce(acc);
+  long long tot = block_reduce(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// in-place inclusive scan of doubles with tile partials
-__global__ void __launch_bounds__(PLAN_THREADS) tile_incl_scan_kernel(double* __restrict__ x, long long n,
-                                                                      const double* __restrict__ part) {
+// in-place inclusive scan of int64 with tile partials
+__global__ void __launch_bounds__(PLAN_THREADS) tile_incl_scan_i64_kernel(long long* __restrict__ x, long long n,
+                                                                          const long long* __restrict__ part) {
   long long i0 = blockIdx.x * (long long)SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
-  double v[SCAN_ITEMS];
-  double loc = 0.0;
+  long long v[SCAN_ITEMS];
+  long long loc = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    v[k] = i0 + k < n ? x[i0 + k] : 0.0;
+    v[k] = i0 + k < n ? x[i0 + k] : 0;
     loc += v[k];
   }
-  double tot;
-  double run = block_excl_scan(loc, &tot) + part[blockIdx.x];
+  long long tot;
+  long long run = block_excl_scan(loc, &tot) + part[blockIdx.x];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
     run += v[k];
@@ -411,43 +422,55 @@ __global__ void __launch_bounds__(PLAN_THREADS) tile_incl_scan_kernel(double* __
   }
 }
 
-// Eq. 3: task t starts at the first item with C_i >= t * Zbar, i.e. item i
-// starts the tasks floor(C_{i-1}/Zbar)+1 .. floor(C_i/Zbar) (the paper's
-// Find-Boundaries criterion floor(C_m/Zbar) != floor(C_{m+1}/Zbar)).
-__global__ void __launch_bounds__(PLAN_THREADS) task_bounds_kernel(const double* __restrict__ C, long long n_items,
-                                                                   long long* __restrict__ task_start, int T) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i == 0) {
+// Eq. 3: the lower boundary of task t is the first item whose inclusive
+// cumulative cost reaches t * Zbar, Zbar = C_total / T, i.e. the first i with
+// C_i * T >= t * C_total -- compared exactly in 128-bit integers.
+__global__ void task_bounds_kernel(const long long* __restrict__ C, long long n_items,
+                                   long long* __restrict__ task_start, int T) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t > T) return;
+  if (t == 0) {
     task_start[0] = 0;
-    task_start[T] = n_items;
+    return;
   }
-  if (i >= n_items) return;
-  double Zbar = C[n_items - 1] / (double)T;
-  double qp = i > 0 ? C[i - 1] / Zbar : 0.0;
-  double q = C[i] / Zbar;
-  long long t0 = (long long)floor(qp) + 1, t1 = (long long)floor(q);
-  if (t1 > T - 1) t1 = T - 1;
-  for (long long t = t0; t <= t1; ++t) task_start[t] = i;
+  if (t == T) {
+    task_start[T] = n_items;
+    return;
+  }
+  const unsigned __int128 goal = (unsigned __int128)(unsigned long long)t * (unsigned long long)C[n_items - 1];
+  long long lo = 0, hi = n_items;  // first i in [lo, hi) with C_i * T >= goal
+  while (lo < hi) {
+    long long mid = (lo + hi) >> 1;
+    if ((unsigned __int128)(unsigned long long)C[mid] * (unsigned long long)T >= goal)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  task_start[t] = lo;
 }
 
 long long scan_partials_needed(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
-void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, const double* d_P, double* d_C,
-                            double* d_partials, long long* d_task_start, int T, int* d_slot32, int tiny_slots,
-                            cudaStream_t s) {
+void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, bool f64, const void* d_P,
+                            long long* d_C, long long* d_partials, long long* d_task_start, int T, int* d_slot32,
+                            int tiny_slots, cudaStream_t s) {
   if (n_items <= 0) {
     // empty plan: a single empty task
-    long long z[2] = {0, 0};
-    cudaMemcpyAsync(d_task_start, z, sizeof(z), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(d_task_start, 0, 2 * sizeof(long long), s);
     return;
   }
   unsigned nb = (unsigned)((n_items + PLAN_THREADS - 1) / PLAN_THREADS);
-  costs_kernel<<<nb, PLAN_THREADS, 0, s>>>(d_graphs, G, n_items, d_P, d_C, d_slot32, tiny_slots);
+  if (f64)
+    costs_kernel<double><<<nb, PLAN_THREADS, 0, s>>>(d_graphs, G, n_items, (const double*)d_P, d_C, d_slot32,
+                                                     tiny_slots);
+  else
+    costs_kernel<long long><<<nb, PLAN_THREADS, 0, s>>>(d_graphs, G, n_items, (const long long*)d_P, d_C, d_slot32,
+                                                        tiny_slots);
   long long nt = (n_items + SCAN_TILE - 1) / SCAN_TILE;
-  tile_reduce_kernel<double><<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
-  partials_scan_kernel<double><<<1, 1024, 0, s>>>(d_partials, nt, nullptr);
-  tile_incl_scan_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
-  task_bounds_kernel<<<nb, PLAN_THREADS, 0, s>>>(d_C, n_items, d_task_start, T);
+  tile_reduce_i64_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
+  partials_scan_kernel<long long><<<1, 1024, 0, s>>>(d_partials, nt, nullptr);
+  tile_incl_scan_i64_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
+  task_bounds_kernel<<<(T + 1 + 255) / 256, 256, 0, s>>>(d_C, n_items, d_task_start, T);
 }
 
 // --------------------------------------------------------------- count scan

@@ -63,8 +63,17 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   const int lane = threadIdx.x & 31;
   const unsigned lanemask_lt = (1u << lane) - 1u;
   long long off_base = 0;
+  bool list_mode = false;  // regeneration driven by the list of items that outgrew their slots
+  long long n_list = 0;
   if (MODE == MODE_EMIT) {
-    if (regen_only && *(volatile int*)P.overflow == 0) return;  // every item fit in its slot
+    if (regen_only) {
+      unsigned nov = *(volatile unsigned*)P.ovf_count;
+      if (nov == 0) return;  // every item fit in its slot
+      if (nov <= P.ovf_cap) {
+        list_mode = true;
+        n_list = nov;
+      }
+    }
     off_base = offsets[ib];
     if (offsets[ie] - off_base > capacity) {
       if (blockIdx.x == 0 && threadIdx.x == 0) set_error(P.err, CL_ERR_CAPACITY);
@@ -102,6 +111,15 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         unsigned tix = 0;
         if (lane == 0) tix = atomicAdd(P.task_ctr, 1u);
         tix = __shfl_sync(FULL_MASK, tix, 0);
+        if (MODE == MODE_EMIT && list_mode) {
+          if ((long long)tix * 32 >= n_list) {
+            tasks_left = false;
+            break;
+          }
+          next = (long long)tix * 32;
+          tend = next + 32 < n_list ? next + 32 : n_list;
+          continue;
+        }
         if (tix >= (unsigned)P.T) {
           tasks_left = false;
           break;
@@ -115,12 +133,17 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       int rank = __popc(need & lanemask_lt);
       int taken = __popc(need);
       if (!have && rank < avail) {
-        item = next + rank;
         have = true;
         fresh = true;
-        if (MODE == MODE_EMIT && regen_only &&
-            offsets[item + 1] - offsets[item] <= P.slot_base[item + 1] - P.slot_base[item])
-          have = fresh = false;  // staged: the copy kernel wrote it
+        if (MODE == MODE_EMIT && list_mode) {
+          item = P.ovf_list[next + rank];
+          if (item < ib || item >= ie) have = fresh = false;
+        } else {
+          item = next + rank;
+          if (MODE == MODE_EMIT && regen_only &&
+              offsets[item + 1] - offsets[item] <= P.slot_base[item + 1] - P.slot_base[item])
+            have = fresh = false;  // staged: the copy kernel wrote it
+        }
       }
       next += taken < avail ? taken : avail;
       need = __ballot_sync(FULL_MASK, !have);
@@ -241,10 +264,15 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         if ((long long)k != expect) set_error(P.err, CL_ERR_DEVICE);
       } else {
         counts[item] = (int)k;
-        if (MODE == MODE_STAGE && k <= ssize) {  // the item's last partial group
-          unsigned c = k & (GROUP - 1);
-          unsigned long long base = sbase + (k & ~(GROUP - 1));
-          for (unsigned i = 0; i < c; ++i) P.pool[base + i] = sgrp[i][threadIdx.x];
+        if (MODE == MODE_STAGE) {
+          if (k <= ssize) {  // the item's last partial group
+            unsigned c = k & (GROUP - 1);
+            unsigned long long base = sbase + (k & ~(GROUP - 1));
+            for (unsigned i = 0; i < c; ++i) P.pool[base + i] = sgrp[i][threadIdx.x];
+          } else {  // remember it for the regeneration pass
+            unsigned idx = atomicAdd(P.ovf_count, 1u);
+            if (idx < P.ovf_cap) P.ovf_list[idx] = item;
+          }
         }
       }
       have = false;
@@ -382,6 +410,7 @@ void launch_count(const DevPlan& P, const DevGraph* single, int* d_counts, bool 
   cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
   if (stage) {
     cudaMemsetAsync(P.overflow, 0, sizeof(int), s);
+    cudaMemsetAsync(P.ovf_count, 0, sizeof(unsigned), s);
     launch_sampler<MODE_STAGE, int2>(P, single, 0, P.n_items, nullptr, nullptr, 0, d_counts, 0, block, grid, s);
   } else {
     launch_sampler<MODE_COUNT, int2>(P, single, 0, P.n_items, nullptr, nullptr, 0, d_counts, 0, block, grid, s);

@@ -238,3 +238,19 @@ def test_parity_config2_counts_full_edges_sampled():
     for (a, b), (_, eo) in zip(ranges, eparts):
         assert np.array_equal(Eh[off[a]:off[b]].astype(np.int64), eo), (a, b)
     g.close()
+
+
+def test_regeneration_beyond_the_overflow_list():
+    """With 8-entry slots, over 2^20 items outgrow their slot: the regeneration
+    pass then walks every item instead of the list; output unchanged."""
+    w = inputs.constant_weights(1_600_000, 60)
+    ref, cref, _ = gpu_generate(w, 13, no_stage=1)
+    E, c, _ = gpu_generate(w, 13, stage_factor=-1.0)
+    assert int((c > 8).sum()) > (1 << 20)
+    assert np.array_equal(c, cref)
+    assert np.array_equal(E, ref)
+    o = oracle.Graph(w, 13)
+    rng = np.random.default_rng(1)
+    for a in rng.integers(0, o.n_items - 20, 10):
+        off = np.concatenate([[0], np.cumsum(cref.astype(np.int64))])
+        assert np.array_equal(E[off[a]:off[a + 20]], o.generate(int(a), int(a) + 20))
