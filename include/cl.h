@@ -192,6 +192,44 @@ cl_status cl_generate_batch(cl_plan* plan, int32_t etype, void* d_edges, int64_t
                             int64_t* d_graph_offsets, int32_t* d_counts, int64_t* d_offsets,
                             int32_t* d_status, cl_stream_t stream);
 
+/* --- expected degrees and weight calibration (Section 3: E[d_i] = w_i - w_i^2/S
+ *     without capping; with the cap min(1, .) of Algorithm 1,
+ *     E_u = sum_{v != u} min(1, w_u w_v / S), S = sum w) ----------------------
+ * Weights are doubles sorted non-increasing (CL_W_F64 convention: the pair is
+ * capped iff fl(w_u w_v) >= S).  S <= 0 means "compute S = sum w on the device
+ * (double-double, rounded once)"; the call then synchronizes to read it. */
+typedef struct {
+  double tol;          /* stop when max_u |E_u - d_u| / d_u <= tol; 0 = 1e-9 */
+  int32_t max_iter;    /* 0 = 100 */
+  int32_t init_from_w; /* 1: start from the weights in d_w; 0: start from the targets */
+} cl_calib_opts;
+
+typedef struct {
+  int32_t iterations;  /* gradient steps taken */
+  double max_rel_err;  /* max_u |E_u - d_u| / d_u at the returned weights */
+  double S;            /* sum of the returned weights */
+} cl_calib_report;
+
+size_t cl_expected_degree_workspace_bytes(int64_t n);
+/* d_E[u] = E_u for the n weights d_w (device arrays of n doubles). */
+cl_status cl_expected_degree(const double* d_w, int64_t n, double S, double* d_E, void* d_ws, size_t ws_bytes,
+                             cl_stream_t stream);
+/* d_gw = gradient of L = sum_u d_gE[u] E_u(w) with respect to w, S = sum w included:
+ * d_gw[k] = [gE_k A_k + sum_{u != k, (u,k) uncapped} gE_u w_u - K] / S with
+ * A_u = sum_{v != u, uncapped} w_v and K = sum_u gE_u (w_u / S) A_u. */
+cl_status cl_expected_degree_adjoint(const double* d_w, const double* d_gE, int64_t n, double S, double* d_gw,
+                                     void* d_ws, size_t ws_bytes, cl_stream_t stream);
+size_t cl_calibrate_workspace_bytes(int64_t n);
+/* Fits d_w so that E(w) matches the target degrees d_target (n doubles, sorted
+ * non-increasing, positive) by preconditioned gradient descent on
+ * L = sum_u (E_u - d_u)^2 / d_u: each step w <- w - g / H with g = dL/dw (the
+ * adjoint above) and the diagonal Gauss-Newton preconditioner
+ * H_u = 2 (dE_u/dw_u)^2 / d_u, dE_u/dw_u = A_u / S; w is kept positive and
+ * non-increasing.  SYNCHRONIZING (one read-back per step).  Returns CL_OK when
+ * max relative error <= tol, else CL_ERR_RANGE with the best weights reached. */
+cl_status cl_calibrate(const double* d_target, int64_t n, double* d_w, const cl_calib_opts* opts,
+                       cl_calib_report* report, void* d_ws, size_t ws_bytes, cl_stream_t stream);
+
 /* SYNCHRONIZING: the run statistics of the last cl_count (flagged skips) and
  * the device error word; resets the counters. */
 cl_status cl_stats(cl_plan* plan, cl_run_stats* out, cl_stream_t stream);

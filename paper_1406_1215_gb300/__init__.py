@@ -48,6 +48,14 @@ class cl_graph_info(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class cl_calib_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("init_from_w", ctypes.c_int32)]
+
+
+class cl_calib_report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("max_rel_err", ctypes.c_double), ("S", ctypes.c_double)]
+
+
 class cl_run_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("ties", ctypes.c_int64),
                 ("error", ctypes.c_int32)]
@@ -87,12 +95,13 @@ def load_library(path: str | None = None):
         "cl_diag_neglog": ([vp, vp, i64, vp, vp, vp], i32),
         "cl_diag_skip": ([vp, vp, vp, vp, i64, vp, vp, vp], i32),
         "cl_scan_noalloc": ([vp, i64, vp, vp], i32),
-    }
-    optional = {
-        "cl_expected_degree": ([vp, i64, ctypes.c_double, vp, vp], i32),
-        "cl_expected_degree_adjoint": ([vp, vp, i64, ctypes.c_double, vp, vp, vp], i32),
         "cl_expected_degree_workspace_bytes": ([i64], sz),
+        "cl_expected_degree": ([vp, i64, ctypes.c_double, vp, vp, sz, vp], i32),
+        "cl_expected_degree_adjoint": ([vp, vp, i64, ctypes.c_double, vp, vp, sz, vp], i32),
+        "cl_calibrate_workspace_bytes": ([i64], sz),
+        "cl_calibrate": ([vp, i64, vp, P(cl_calib_opts), P(cl_calib_report), vp, sz, vp], i32),
     }
+    optional = {}
     for name, (args, res) in list(sig.items()) + list(optional.items()):
         if not hasattr(L, name):
             if name in optional:
@@ -207,6 +216,34 @@ def cl_check(plan, stream=None) -> int:
 def cl_plan_destroy(plan):
     if plan:
         load_library().cl_plan_destroy(plan)
+
+
+def cl_expected_degree_workspace_bytes(n: int) -> int:
+    return load_library().cl_expected_degree_workspace_bytes(n)
+
+
+def cl_expected_degree(d_w, n: int, S: float, d_E, d_ws, ws_bytes: int, stream=None):
+    _check(load_library().cl_expected_degree(_ptr(d_w), n, S, _ptr(d_E), _ptr(d_ws), ws_bytes, _stream(stream)),
+           "cl_expected_degree")
+
+
+def cl_expected_degree_adjoint(d_w, d_gE, n: int, S: float, d_gw, d_ws, ws_bytes: int, stream=None):
+    _check(load_library().cl_expected_degree_adjoint(_ptr(d_w), _ptr(d_gE), n, S, _ptr(d_gw), _ptr(d_ws), ws_bytes,
+                                                     _stream(stream)), "cl_expected_degree_adjoint")
+
+
+def cl_calibrate_workspace_bytes(n: int) -> int:
+    return load_library().cl_calibrate_workspace_bytes(n)
+
+
+def cl_calibrate(d_target, n: int, d_w, opts: cl_calib_opts | None, d_ws, ws_bytes: int, stream=None):
+    """Returns (status, report); status CL_ERR_RANGE means the tolerance was not reached."""
+    rep = cl_calib_report()
+    st = load_library().cl_calibrate(_ptr(d_target), n, _ptr(d_w), ctypes.byref(opts) if opts else None,
+                                     ctypes.byref(rep), _ptr(d_ws), ws_bytes, _stream(stream))
+    if st not in (CL_OK, 4):
+        raise ClError(st, "cl_calibrate")
+    return st, {"iterations": rep.iterations, "max_rel_err": rep.max_rel_err, "S": rep.S}
 
 
 def cl_scan_noalloc(d_counts, n: int, d_offsets, stream=None):

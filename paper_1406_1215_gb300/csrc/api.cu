@@ -166,6 +166,7 @@ DevPlan dev_plan(const cl_plan* p) {
   P.ovf_list = p->d_ovf_list;
   P.ovf_count = p->d_ovf_count;
   P.ovf_cap = OVF_CAP;
+  P.wf64 = p->wtype == CL_W_F64 ? 1 : 0;
   return P;
 }
 

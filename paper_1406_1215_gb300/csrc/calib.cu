@@ -1,0 +1,546 @@
+// calib.cu -- capped expected degrees, their adjoint, and weight calibration.
+//
+// Section 3: with no capped pair the expected degree of node i is
+// w_i - w_i^2/S.  With the cap min(1, .) of Algorithm 1 it is
+//   E_u = sum_{v != u} min(1, w_u w_v / S),   S = sum_k w_k.
+// For w sorted non-increasing the capped partners of u (fl(w_u w_v) >= S) are
+// a prefix [0, t_u), so with R_k = sum_{v >= k} w_v
+//   E_u = (t_u - [u < t_u]) + (w_u / S) A_u,   A_u = R_{t_u} - [u >= t_u] w_u.
+// The gradient of L = sum_u gE_u E_u (S depends on w):
+//   dL/dw_k = [gE_k A_k + B_k - K] / S,  B_k = G_{t_k} - [k >= t_k] gE_k w_k,
+//   G_j = sum_{u >= j} gE_u w_u,  K = sum_u gE_u (w_u / S) A_u.
+// Suffix sums and reductions are carried in double-double; the per-node terms
+// are rounded once to double.  FP64 is slow on this GPU (1/75 of FP32), but
+// these kernels make O(n log n) FP64 operations over a few arrays.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cl_internal.cuh"
+#include "clmath.cuh"
+
+namespace cl {
+namespace {
+
+constexpr int CT = 256;            // threads per block
+constexpr int CI = 8;              // items per thread in a scan tile
+constexpr int CTILE = CT * CI;
+
+__device__ __forceinline__ dd dd_shfl_up(dd v, int o) {
+  return dd{__shfl_up_sync(FULL_MASK, v.hi, o), __shfl_up_sync(FULL_MASK, v.lo, o)};
+}
+__device__ __forceinline__ dd dd_shfl_xor(dd v, int o) {
+  return dd{__shfl_xor_sync(FULL_MASK, v.hi, o), __shfl_xor_sync(FULL_MASK, v.lo, o)};
+}
+
+__device__ __forceinline__ dd dd_block_reduce(dd v) {
+  __shared__ double rh[32], rl[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = dd_add(v, dd_shfl_xor(v, o));
+  if (lane == 0) {
+    rh[wid] = v.hi;
+    rl[wid] = v.lo;
+  }
+  __syncthreads();
+  dd t{0.0, 0.0};
+  if (wid == 0) {
+    if (lane < nw) t = dd{rh[lane], rl[lane]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = dd_add(t, dd_shfl_xor(t, o));
+  }
+  __syncthreads();
+  return t;  // valid in warp 0
+}
+
+// exclusive block scan of dd values (one per thread); total in *tot
+__device__ __forceinline__ dd dd_block_excl(dd v, dd* tot) {
+  __shared__ double sh[32], sl[32];
+  __shared__ double th, tl;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  dd inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    dd y = dd_shfl_up(inc, o);
+    if (lane >= o) inc = dd_add(inc, y);
+  }
+  if (lane == 31) {
+    sh[wid] = inc.hi;
+    sl[wid] = inc.lo;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    dd t = lane < nw ? dd{sh[lane], sl[lane]} : dd{0.0, 0.0};
+    dd ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      dd y = dd_shfl_up(ti, o);
+      if (lane >= o) ti = dd_add(ti, y);
+    }
+    dd ex = dd_add(ti, dd{-t.hi, -t.lo});
+    if (lane < nw) {
+      sh[lane] = ex.hi;
+      sl[lane] = ex.lo;
+    }
+    if (lane == nw - 1) {
+      th = ti.hi;
+      tl = ti.lo;
+    }
+  }
+  __syncthreads();
+  dd res = dd_add(dd{sh[wid], sl[wid]}, dd_add(inc, dd{-v.hi, -v.lo}));
+  *tot = dd{th, tl};
+  __syncthreads();
+  return res;
+}
+
+// x_i of a suffix sum: w_i, or the exact product gE_i w_i
+__device__ __forceinline__ dd term(const double* a, const double* b, long long i) {
+  return b ? dd_two_prod(a[i], b[i]) : dd{a[i], 0.0};
+}
+
+// Suffix sums R[k] = sum_{i >= k} x_i, k = 0..n (R[n] = 0), computed on the
+// reversed index j = n-1-i as an inclusive prefix: tile sums, their scan, tile scan.
+__global__ void __launch_bounds__(CT) suffix_reduce_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                           long long n, double* __restrict__ part) {
+  long long j0 = blockIdx.x * (long long)CTILE;
+  dd acc{0.0, 0.0};
+  for (int k = 0; k < CI; ++k) {
+    long long j = j0 + (long long)k * CT + threadIdx.x;
+    if (j < n) acc = dd_add(acc, term(a, b, n - 1 - j));
+  }
+  dd t = dd_block_reduce(acc);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t.hi;
+    part[2 * blockIdx.x + 1] = t.lo;
+  }
+}
+
+__global__ void suffix_partials_kernel(double* __restrict__ part, long long nt) {
+  __shared__ double ch, cl_;
+  if (threadIdx.x == 0) ch = cl_ = 0.0;
+  __syncthreads();
+  for (long long base = 0; base < nt; base += blockDim.x) {
+    long long i = base + threadIdx.x;
+    dd v = i < nt ? dd{part[2 * i], part[2 * i + 1]} : dd{0.0, 0.0};
+    dd carry{ch, cl_};
+    dd tot;
+    dd ex = dd_add(dd_block_excl(v, &tot), carry);
+    if (i < nt) {
+      part[2 * i] = ex.hi;
+      part[2 * i + 1] = ex.lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      dd c = dd_add(carry, tot);
+      ch = c.hi;
+      cl_ = c.lo;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(CT) suffix_scan_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                         long long n, const double* __restrict__ part,
+                                                         double* __restrict__ R) {
+  long long j0 = blockIdx.x * (long long)CTILE + (long long)threadIdx.x * CI;
+  dd v[CI];
+  dd loc{0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < CI; ++k) {
+    v[k] = (j0 + k < n) ? term(a, b, n - 1 - (j0 + k)) : dd{0.0, 0.0};
+    loc = dd_add(loc, v[k]);
+  }
+  dd tot;
+  dd run = dd_add(dd_block_excl(loc, &tot), dd{part[2 * blockIdx.x], part[2 * blockIdx.x + 1]});
+#pragma unroll
+  for (int k = 0; k < CI; ++k) {
+    run = dd_add(run, v[k]);  // inclusive prefix over reversed index = sum_{i >= n-1-j}
+    long long j = j0 + k;
+    if (j < n) {
+      long long i = n - 1 - j;
+      R[2 * i] = run.hi;
+      R[2 * i + 1] = run.lo;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    R[2 * n] = 0.0;
+    R[2 * n + 1] = 0.0;
+  }
+}
+
+void suffix_sums(const double* a, const double* b, long long n, double* part, double* R, cudaStream_t s) {
+  long long nt = (n + CTILE - 1) / CTILE;
+  if (n <= 0) {
+    cudaMemsetAsync(R, 0, 2 * sizeof(double), s);
+    return;
+  }
+  suffix_reduce_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, part);
+  suffix_partials_kernel<<<1, 1024, 0, s>>>(part, nt);
+  suffix_scan_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, part, R);
+}
+
+// t_u = #{v : fl(w_u w_v) >= S}: the capped partners form a prefix of the sorted w.
+__device__ __forceinline__ long long cap_threshold(const double* w, long long n, double wu, double S) {
+  long long lo = 0, hi = n;
+  while (lo < hi) {
+    long long mid = (lo + hi) >> 1;
+    if (wu * w[mid] >= S)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// forward: E_u, and per node t_u and A_u / S (the uncapped part's derivative dE_u/dw_u at fixed S)
+__global__ void __launch_bounds__(CT) expdeg_kernel(const double* __restrict__ w, long long n, double S,
+                                                    const double* __restrict__ R, double* __restrict__ E,
+                                                    long long* __restrict__ tcap, double* __restrict__ Ahi,
+                                                    double* __restrict__ Alo) {
+  long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  double wu = w[u];
+  long long t = cap_threshold(w, n, wu, S);
+  dd A{R[2 * t], R[2 * t + 1]};
+  if (u >= t) A = dd_add(A, dd{-wu, 0.0});
+  dd part = dd_div(dd_mul_d(A, wu), dd{S, 0.0});  // (w_u / S) A_u
+  double capped = (double)(t - (u < t ? 1 : 0));
+  dd e = dd_add(part, dd{capped, 0.0});
+  if (E) E[u] = e.hi + e.lo;
+  if (tcap) tcap[u] = t;
+  if (Ahi) {
+    Ahi[u] = A.hi;
+    Alo[u] = A.lo;
+  }
+}
+
+// K = sum_u gE_u (w_u / S) A_u (block partial sums, dd)
+__global__ void __launch_bounds__(CT) adj_K_kernel(const double* __restrict__ w, const double* __restrict__ gE,
+                                                   long long n, double S, const double* __restrict__ Ahi,
+                                                   const double* __restrict__ Alo, double* __restrict__ part) {
+  long long i0 = blockIdx.x * (long long)CTILE;
+  dd acc{0.0, 0.0};
+  for (int k = 0; k < CI; ++k) {
+    long long u = i0 + (long long)k * CT + threadIdx.x;
+    if (u < n) {
+      dd A{Ahi[u], Alo[u]};
+      acc = dd_add(acc, dd_mul_d(dd_mul_d(A, w[u]), gE[u]));
+    }
+  }
+  dd t = dd_block_reduce(acc);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t.hi;
+    part[2 * blockIdx.x + 1] = t.lo;
+  }
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ part, long long nt, double S, double* __restrict__ out) {
+  dd acc{0.0, 0.0};
+  for (long long i = threadIdx.x; i < nt; i += blockDim.x) acc = dd_add(acc, dd{part[2 * i], part[2 * i + 1]});
+  dd t = dd_block_reduce(acc);
+  if (threadIdx.x == 0) {
+    dd K = dd_div(t, dd{S, 0.0});
+    out[0] = K.hi;
+    out[1] = K.lo;
+  }
+}
+
+__global__ void __launch_bounds__(CT) adj_grad_kernel(const double* __restrict__ w, const double* __restrict__ gE,
+                                                      long long n, double S, const long long* __restrict__ tcap,
+                                                      const double* __restrict__ Ahi, const double* __restrict__ Alo,
+                                                      const double* __restrict__ G, const double* __restrict__ Kp,
+                                                      double* __restrict__ gw) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  long long t = tcap[k];
+  dd A{Ahi[k], Alo[k]};
+  dd B{G[2 * t], G[2 * t + 1]};
+  if (k >= t) {
+    dd gw_k = dd_two_prod(gE[k], w[k]);
+    B = dd_add(B, dd{-gw_k.hi, -gw_k.lo});
+  }
+  dd num = dd_add(dd_add(dd_mul_d(A, gE[k]), B), dd{-Kp[0], -Kp[1]});
+  dd r = dd_div(num, dd{S, 0.0});
+  gw[k] = r.hi + r.lo;
+}
+
+// S = sum w in double-double, rounded once (block partials, then one block)
+__global__ void __launch_bounds__(CT) sum_reduce_kernel(const double* __restrict__ w, long long n,
+                                                        double* __restrict__ part) {
+  long long i0 = blockIdx.x * (long long)CTILE;
+  dd acc{0.0, 0.0};
+  for (int k = 0; k < CI; ++k) {
+    long long i = i0 + (long long)k * CT + threadIdx.x;
+    if (i < n) acc = dd_add(acc, dd{w[i], 0.0});
+  }
+  dd t = dd_block_reduce(acc);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t.hi;
+    part[2 * blockIdx.x + 1] = t.lo;
+  }
+}
+
+__global__ void sum_final_kernel(const double* __restrict__ part, long long nt, double* __restrict__ out) {
+  dd acc{0.0, 0.0};
+  for (long long i = threadIdx.x; i < nt; i += blockDim.x) acc = dd_add(acc, dd{part[2 * i], part[2 * i + 1]});
+  dd t = dd_block_reduce(acc);
+  if (threadIdx.x == 0) out[0] = t.hi + t.lo;
+}
+
+// one calibration step, per node: max relative error of E against the target,
+// then the preconditioned gradient step w - g / H, H = 2 J^2 / d, J = A / S
+__global__ void __launch_bounds__(CT) relerr_kernel(const double* __restrict__ E, const double* __restrict__ d,
+                                                    long long n, unsigned long long* __restrict__ maxbits,
+                                                    double* __restrict__ gE) {
+  long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double r = 0.0;
+  if (u < n) {
+    double diff = E[u] - d[u];
+    r = fabs(diff) / d[u];
+    gE[u] = 2.0 * diff / d[u];  // dL/dE for L = sum (E - d)^2 / d
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(FULL_MASK, r, o));
+  if ((threadIdx.x & 31) == 0 && r > 0.0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(r));
+}
+
+__global__ void __launch_bounds__(CT) step_kernel(double* __restrict__ w, const double* __restrict__ d,
+                                                  const double* __restrict__ g, const double* __restrict__ Ahi,
+                                                  long long n, double S) {
+  long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  double J = Ahi[u] / S;
+  J = J > 1e-300 ? J : 1e-300;
+  double H = 2.0 * J * J / d[u];
+  double wn = w[u] - g[u] / H;
+  double floor_ = 1e-9 * d[u];
+  w[u] = wn > floor_ ? wn : floor_;
+}
+
+// keep w non-increasing: w_u <- min_{v <= u} w_v (a running minimum, one block per tile + carry)
+__global__ void __launch_bounds__(CT) runmin_tile_kernel(const double* __restrict__ w, long long n,
+                                                         double* __restrict__ part) {
+  long long i0 = blockIdx.x * (long long)CTILE;
+  double m = INFINITY;
+  for (int k = 0; k < CI; ++k) {
+    long long i = i0 + (long long)k * CT + threadIdx.x;
+    if (i < n) m = fmin(m, w[i]);
+  }
+  __shared__ double sm[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(FULL_MASK, m, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = INFINITY;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmin(t, sm[k]);
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void runmin_partials_kernel(double* __restrict__ part, long long nt) {
+  if (threadIdx.x != 0) return;
+  double m = INFINITY;
+  for (long long i = 0; i < nt; ++i) {  // exclusive running minimum of the tile minima
+    double v = part[i];
+    part[i] = m;
+    m = fmin(m, v);
+  }
+}
+
+__global__ void __launch_bounds__(CT) runmin_apply_kernel(double* __restrict__ w, long long n,
+                                                          const double* __restrict__ part) {
+  long long i0 = blockIdx.x * (long long)CTILE + (long long)threadIdx.x * CI;
+  double v[CI];
+  double loc = INFINITY;
+#pragma unroll
+  for (int k = 0; k < CI; ++k) {
+    v[k] = i0 + k < n ? w[i0 + k] : INFINITY;
+    loc = fmin(loc, v[k]);
+  }
+  // exclusive running minimum across the block's threads
+  __shared__ double sm[CT];
+  sm[threadIdx.x] = loc;
+  __syncthreads();
+  for (int o = 1; o < CT; o <<= 1) {
+    double y = threadIdx.x >= (unsigned)o ? sm[threadIdx.x - o] : INFINITY;
+    __syncthreads();
+    sm[threadIdx.x] = fmin(sm[threadIdx.x], y);
+    __syncthreads();
+  }
+  double run = threadIdx.x > 0 ? sm[threadIdx.x - 1] : INFINITY;
+  run = fmin(run, part[blockIdx.x]);
+#pragma unroll
+  for (int k = 0; k < CI; ++k) {
+    run = fmin(run, v[k]);
+    if (i0 + k < n) w[i0 + k] = run;
+  }
+}
+
+struct CalWs {
+  double* R;      // 2 (n + 1)
+  double* G;      // 2 (n + 1)
+  long long* t;   // n
+  double* Ahi;    // n
+  double* Alo;    // n
+  double* part;   // 2 tiles
+  double* scal;   // 8: S, K (2), ...
+  unsigned long long* maxbits;
+  double* E;      // n (calibration)
+  double* gE;     // n (calibration)
+  double* g;      // n (calibration)
+  size_t bytes;
+};
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+CalWs cal_layout(void* base, long long n, bool calib) {
+  char* b = (char*)base;
+  size_t off = 0;
+  CalWs L;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = b ? (void*)(b + off) : nullptr;
+    off += al(bytes);
+    return p;
+  };
+  long long nt = (n + CTILE - 1) / CTILE + 1;
+  L.R = (double*)take(sizeof(double) * 2 * (n + 1));
+  L.G = (double*)take(sizeof(double) * 2 * (n + 1));
+  L.t = (long long*)take(sizeof(long long) * (n > 0 ? n : 1));
+  L.Ahi = (double*)take(sizeof(double) * (n > 0 ? n : 1));
+  L.Alo = (double*)take(sizeof(double) * (n > 0 ? n : 1));
+  L.part = (double*)take(sizeof(double) * 2 * nt);
+  L.scal = (double*)take(sizeof(double) * 8);
+  L.maxbits = (unsigned long long*)take(sizeof(unsigned long long) * 2);
+  L.E = calib ? (double*)take(sizeof(double) * (n > 0 ? n : 1)) : nullptr;
+  L.gE = calib ? (double*)take(sizeof(double) * (n > 0 ? n : 1)) : nullptr;
+  L.g = calib ? (double*)take(sizeof(double) * (n > 0 ? n : 1)) : nullptr;
+  L.bytes = off;
+  return L;
+}
+
+void device_sum(const double* w, long long n, double* part, double* out, cudaStream_t s) {
+  long long nt = (n + CTILE - 1) / CTILE;
+  if (nt < 1) nt = 1;
+  sum_reduce_kernel<<<(unsigned)nt, CT, 0, s>>>(w, n, part);
+  sum_final_kernel<<<1, 1024, 0, s>>>(part, nt, out);
+}
+
+unsigned nblk(long long n) { return (unsigned)((n + CT - 1) / CT); }
+
+void forward(const double* w, long long n, double S, double* E, const CalWs& L, cudaStream_t s) {
+  suffix_sums(w, nullptr, n, L.part, L.R, s);
+  expdeg_kernel<<<nblk(n), CT, 0, s>>>(w, n, S, L.R, E, L.t, L.Ahi, L.Alo);
+}
+
+void adjoint(const double* w, const double* gE, long long n, double S, double* gw, const CalWs& L, cudaStream_t s) {
+  long long nt = (n + CTILE - 1) / CTILE;
+  suffix_sums(gE, w, n, L.part, L.G, s);
+  adj_K_kernel<<<(unsigned)nt, CT, 0, s>>>(w, gE, n, S, L.Ahi, L.Alo, L.part);
+  sum_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt, S, L.scal + 2);
+  adj_grad_kernel<<<nblk(n), CT, 0, s>>>(w, gE, n, S, L.t, L.Ahi, L.Alo, L.G, L.scal + 2, gw);
+}
+
+}  // namespace
+}  // namespace cl
+
+using namespace cl;
+
+static cl_status ok_last() { return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA; }
+
+extern "C" size_t cl_expected_degree_workspace_bytes(int64_t n) {
+  if (n < 0) return 0;
+  return cal_layout(nullptr, n, false).bytes;
+}
+
+extern "C" size_t cl_calibrate_workspace_bytes(int64_t n) {
+  if (n < 0) return 0;
+  return cal_layout(nullptr, n, true).bytes;
+}
+
+static cl_status resolve_S(const double* d_w, int64_t n, double S, const CalWs& L, cudaStream_t s, double* out) {
+  if (S > 0) {
+    *out = S;
+    return CL_OK;
+  }
+  device_sum(d_w, n, L.part, L.scal, s);
+  if (cudaMemcpyAsync(out, L.scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CL_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+  return *out > 0 ? CL_OK : CL_ERR_RANGE;
+}
+
+extern "C" cl_status cl_expected_degree(const double* d_w, int64_t n, double S, double* d_E, void* d_ws,
+                                        size_t ws_bytes, cl_stream_t stream) {
+  if (n < 0 || (n > 0 && (!d_w || !d_E))) return CL_ERR_INVALID_ARG;
+  if (n == 0) return CL_OK;
+  CalWs L = cal_layout(d_ws, n, false);
+  if (!d_ws || ws_bytes < L.bytes) return CL_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cl_status st = resolve_S(d_w, n, S, L, s, &S);
+  if (st != CL_OK) return st;
+  forward(d_w, n, S, d_E, L, s);
+  return ok_last();
+}
+
+extern "C" cl_status cl_expected_degree_adjoint(const double* d_w, const double* d_gE, int64_t n, double S,
+                                                double* d_gw, void* d_ws, size_t ws_bytes, cl_stream_t stream) {
+  if (n < 0 || (n > 0 && (!d_w || !d_gE || !d_gw))) return CL_ERR_INVALID_ARG;
+  if (n == 0) return CL_OK;
+  CalWs L = cal_layout(d_ws, n, false);
+  if (!d_ws || ws_bytes < L.bytes) return CL_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cl_status st = resolve_S(d_w, n, S, L, s, &S);
+  if (st != CL_OK) return st;
+  // the forward quantities (R, t, A) the adjoint needs
+  suffix_sums(d_w, nullptr, n, L.part, L.R, s);
+  expdeg_kernel<<<nblk(n), CT, 0, s>>>(d_w, n, S, L.R, nullptr, L.t, L.Ahi, L.Alo);
+  adjoint(d_w, d_gE, n, S, d_gw, L, s);
+  return ok_last();
+}
+
+extern "C" cl_status cl_calibrate(const double* d_target, int64_t n, double* d_w, const cl_calib_opts* opts,
+                                  cl_calib_report* report, void* d_ws, size_t ws_bytes, cl_stream_t stream) {
+  if (n <= 0 || !d_target || !d_w) return CL_ERR_INVALID_ARG;
+  CalWs L = cal_layout(d_ws, n, true);
+  if (!d_ws || ws_bytes < L.bytes) return CL_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  double tol = (opts && opts->tol > 0) ? opts->tol : 1e-9;
+  int max_iter = (opts && opts->max_iter > 0) ? opts->max_iter : 100;
+  if (!(opts && opts->init_from_w))
+    if (cudaMemcpyAsync(d_w, d_target, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return CL_ERR_CUDA;
+  long long nt = (n + CTILE - 1) / CTILE;
+  double S = 0, maxrel = INFINITY;
+  int it = 0;
+  for (;; ++it) {
+    device_sum(d_w, n, L.part, L.scal, s);
+    cudaMemsetAsync(L.maxbits, 0, sizeof(unsigned long long), s);
+    double hostS = 0;
+    unsigned long long bits = 0;
+    // S must be known on the host for the kernels' arguments
+    if (cudaMemcpyAsync(&hostS, L.scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+    S = hostS;
+    forward(d_w, n, S, L.E, L, s);
+    relerr_kernel<<<nblk(n), CT, 0, s>>>(L.E, d_target, n, L.maxbits, L.gE);
+    if (cudaMemcpyAsync(&bits, L.maxbits, sizeof(bits), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+    std::memcpy(&maxrel, &bits, sizeof(double));
+    if (maxrel <= tol || it >= max_iter) break;
+    adjoint(d_w, L.gE, n, S, L.g, L, s);
+    step_kernel<<<nblk(n), CT, 0, s>>>(d_w, d_target, L.g, L.Ahi, n, S);
+    runmin_tile_kernel<<<(unsigned)nt, CT, 0, s>>>(d_w, n, L.part);
+    runmin_partials_kernel<<<1, 32, 0, s>>>(L.part, nt);
+    runmin_apply_kernel<<<(unsigned)nt, CT, 0, s>>>(d_w, n, L.part);
+    if (ok_last() != CL_OK) return CL_ERR_CUDA;
+  }
+  if (report) {
+    report->iterations = it;
+    report->max_rel_err = maxrel;
+    report->S = S;
+  }
+  return maxrel <= tol ? CL_OK : CL_ERR_RANGE;
+}

@@ -105,6 +105,7 @@ struct DevPlan {
   long long* ovf_list;          // items that outgrew their slot (first ovf_cap of them)
   unsigned* ovf_count;
   unsigned ovf_cap;
+  int wf64;                     // the plan's weights are doubles
 };
 
 // ---- launchers implemented in plan.cu / sample.cu / diag.cu ----

@@ -305,10 +305,11 @@ __device__ __forceinline__ long long floor_decide_ff(ff x, long long R) {
   return k;
 }
 
-// Same for double-double with tau = 2^-96; an undecided x takes the nearest
-// integer (*tie = true), which is the exact floor when x is an integer.
+// Same for double-double with tau = 2^-92 (the tier's evaluation error is below
+// 2^-96); an undecided x takes the nearest integer (*tie = true), which is the
+// exact floor when x is an integer.
 __device__ __forceinline__ long long floor_decide_dd(dd x, long long R, bool* tie) {
-  const double tau = 0x1p-96;
+  const double tau = 0x1p-92;
   *tie = false;
   if (x.hi > 0x1p40 || x.hi > (double)R * (1.0 + 0x1p-40)) return R;
   double k0 = floor(x.hi);
@@ -334,6 +335,77 @@ __device__ __forceinline__ long long floor_decide_dd(dd x, long long R, bool* ti
     if (dhi < dlo) k += 1;  // nearest integer
   }
   return k < R ? k : R;
+}
+
+// Tier 1 for double weights: x = L_r / L_p as one double (L_r from float-float,
+// L_p from the double logarithm), window 2^-40 x as for float-float.
+__device__ __forceinline__ long long floor_decide_d(double x, long long R) {
+  const double tau = 0x1p-40;
+  if (!(x < 0x1p33)) return R;
+  double k0 = floor(x);
+  long long k = (long long)k0;
+  if (k > R) return R;
+  double dlo = x - k0;          // exact
+  double dhi = 1.0 - dlo;       // one rounding
+  double margin = tau * x;
+  if (k >= R) return dlo > margin ? R : SKIP_UNDECIDED;
+  if (!(dlo > margin) || !(dhi > margin)) return SKIP_UNDECIDED;
+  return k;
+}
+
+// -ln(1 - Q/S) for doubles 0 < Q < S, in double: log1p(-Q/S) while Q/S <= 1/2,
+// else log((S - Q)/S) with S - Q exact (Sterbenz' lemma).
+__device__ __forceinline__ double d_neglog1m(double Q, double S) {
+  if (2.0 * Q <= S) return -log1p(-(Q / S));
+  return -log((S - Q) / S);
+}
+
+// sum_{k=0}^{9} z^k / (2k+1) times s: atanh(s) in double-double, |s| <~ 2^-7
+__device__ __forceinline__ dd dd_atanh_small(dd s) {
+  dd z = dd_mul(s, s);
+  dd p = dd{__ldg(&CL_ATANH_DD[9][0]), __ldg(&CL_ATANH_DD[9][1])};
+  for (int k = 8; k >= 0; --k) p = dd_add(dd_mul(p, z), dd{__ldg(&CL_ATANH_DD[k][0]), __ldg(&CL_ATANH_DD[k][1])});
+  return dd_mul(s, p);
+}
+
+// -ln(1 - Q/S) for doubles 0 < Q < S, in double-double: y = 1 - Q/S (formed as
+// (1 - c) - Q/S when Q/S <= 1/2, else as (S - Q)/S with S - Q exact), reduced
+// to m = y 2^e in [1/2, 1) and c = J/64, then ln(64/J) + e ln2 - 2 atanh((m-c)/(m+c)).
+static __device__ __noinline__ dd dd_neglog1m_f64(double Q, double S) {
+  int e = 0;
+  int J;
+  dd d, den;
+  if (2.0 * Q <= S) {
+    dd p = dd_div(dd{Q, 0.0}, dd{S, 0.0});
+    J = __double2int_rn(64.0 * (1.0 - p.hi));
+    J = J < 32 ? 32 : (J > 64 ? 64 : J);
+    double c = J / 64.0;
+    d = dd_add(dd{1.0 - c, 0.0}, dd{-p.hi, -p.lo});
+    den = dd_add(dd{2.0 * c, 0.0}, d);
+  } else {
+    dd y = dd_div(dd{S - Q, 0.0}, dd{S, 0.0});
+    int ex;
+    frexp(y.hi, &ex);  // y.hi = f 2^ex, f in [1/2, 1)
+    e = -ex;
+    dd m = dd{ldexp(y.hi, e), ldexp(y.lo, e)};
+    J = __double2int_rn(64.0 * m.hi);
+    J = J < 32 ? 32 : (J > 64 ? 64 : J);
+    double c = J / 64.0;
+    d = dd_add(m, dd{-c, 0.0});
+    den = dd_add(m, dd{c, 0.0});
+  }
+  dd at = dd_atanh_small(dd_div(d, den));
+  dd t = dd{__ldg(&CL_LNT_DD[J - 32][0]), __ldg(&CL_LNT_DD[J - 32][1])};
+  dd le = dd_mul_d(dd{CL_LN2_DD_HI, CL_LN2_DD_LO}, (double)e);
+  return dd_add(dd_add(le, t), dd{-2.0 * at.hi, -2.0 * at.lo});
+}
+
+// Tier-2 skip for double weights.
+static __device__ __noinline__ long long skip_fallback_dd_f64(unsigned long long Ar, double Q, double S, long long R,
+                                                              bool* tie) {
+  dd Lr = dd_neglog_ratio(Ar, 1ull << 53);
+  dd Lp = dd_neglog1m_f64(Q, S);
+  return floor_decide_dd(dd_div(Lr, Lp), R, tie);
 }
 
 // Tier-2 skip: x = -ln(Ar / 2^53) / -ln(Ap / S) in double-double.

@@ -56,10 +56,63 @@ __device__ __forceinline__ bool accept_i(unsigned long long k, unsigned long lon
 // draw; the candidate is then accepted or rejected with the draw it was made
 // with.  Single-graph plans read the graph's parameters from the kernel
 // parameter (constant bank) instead of per-lane registers.
-template <int MODE, bool SINGLE, typename E>
+// Weight types: integer weights work with exact 64-bit products and float-float
+// logarithms; double weights (calibrated sequences) with the rounded product
+// capped at S, the double logarithm for L_p and the exact sign of a fused
+// multiply-add for the acceptance.
+template <bool WF>
+struct Wt;
+template <>
+struct Wt<false> {
+  using w_t = int;
+  using q_t = unsigned long long;
+  using lp_t = ff;
+  static __device__ __forceinline__ q_t S(const DevGraph& g) { return (q_t)g.S_i; }
+  static __device__ __forceinline__ q_t Q(w_t a, w_t b, q_t S) {
+    q_t q = (q_t)((long long)a * (long long)b);
+    return q < S ? q : S;
+  }
+  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, ff Sf) { return ff_neglog1m(Q, S, Sf); }
+  static __device__ __forceinline__ long long skip1(ff Lr, lp_t Lp, long long R) {
+    return floor_decide_ff(ff_div(Lr, Lp), R);
+  }
+  static __device__ __forceinline__ long long skip2(unsigned long long Ar, q_t Q, q_t S, long long R, bool* tie) {
+    return skip_fallback_dd(Ar, S - Q, S, R, tie);
+  }
+  static __device__ __forceinline__ bool accept(unsigned long long k, q_t Qprev, q_t Qv) {
+    return accept_i(k, Qprev, Qv);
+  }
+};
+template <>
+struct Wt<true> {
+  using w_t = double;
+  using q_t = double;
+  using lp_t = double;
+  static __device__ __forceinline__ q_t S(const DevGraph& g) { return g.S_d; }
+  static __device__ __forceinline__ q_t Q(w_t a, w_t b, q_t S) {
+    q_t q = a * b;
+    return q >= S ? S : q;  // capped iff the rounded product reaches S
+  }
+  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, ff) { return d_neglog1m(Q, S); }
+  static __device__ __forceinline__ long long skip1(ff Lr, lp_t Lp, long long R) {
+    return floor_decide_d(((double)Lr.hi + (double)Lr.lo) / Lp, R);
+  }
+  static __device__ __forceinline__ long long skip2(unsigned long long Ar, q_t Q, q_t S, long long R, bool* tie) {
+    return skip_fallback_dd_f64(Ar, Q, S, R, tie);
+  }
+  static __device__ __forceinline__ bool accept(unsigned long long k, q_t Qprev, q_t Qv) {
+    double r = (double)(2ull * k + 1ull) * 0x1p-53;  // exact
+    return fma(r, Qprev, -Qv) < 0.0;                  // the sign of r Qprev - Qv, exactly
+  }
+};
+
+template <int MODE, bool SINGLE, bool WF, typename E>
 __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
     sample_kernel(DevPlan P, DevGraph G1, long long ib, long long ie, const long long* __restrict__ offsets,
                   E* __restrict__ edges, long long capacity, int* __restrict__ counts, int regen_only) {
+  using T = Wt<WF>;
+  using w_t = typename T::w_t;
+  using q_t = typename T::q_t;
   const int lane = threadIdx.x & 31;
   const unsigned lanemask_lt = (1u << lane) - 1u;
   long long off_base = 0;
@@ -87,14 +140,14 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   bool have = false, fresh = false;
   long long item = 0, obase = 0;
   unsigned u = 0, seg = 0, j = 0, end = 0, t = 0, k = 0;
-  unsigned long long Qprev = 0;
-  ff Lp{0.f, 0.f};
-  int wu = 0;
+  q_t Qprev = 0;
+  typename T::lp_t Lp{};
+  w_t wu = 0;
   u32x4 pb{0u, 0u, 0u, 0u};  // the lane's next draw (index t) ...
   ff pLr{0.f, 0.f};          // ... and its -ln r_s
   // graph of the lane's item (batched plans only)
-  const int* w_l = nullptr;
-  unsigned long long S_l = 0;
+  const w_t* w_l = nullptr;
+  q_t S_l = 0;
   float Sh_l = 0.f, Sl_l = 0.f;
   unsigned k0_l = 0, k1_l = 0;
   unsigned long long sbase = 0;  // staging: the item's slot and its size
@@ -164,14 +217,14 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         int gi = graph_of_item(P.graphs, P.G, item);
         const DevGraph& g = P.graphs[gi];
         item_bounds(g, item - g.item_begin, u, seg, j0, end);
-        w_l = (const int*)g.w;
-        S_l = (unsigned long long)g.S_i;
+        w_l = (const w_t*)g.w;
+        S_l = T::S(g);
         Sh_l = g.S_ff_hi;
         Sl_l = g.S_ff_lo;
         k0_l = g.key0;
         k1_l = g.key1;
       }
-      wu = __ldg(&(SINGLE ? (const int*)G1.w : w_l)[u]);
+      wu = __ldg(&(SINGLE ? (const w_t*)G1.w : w_l)[u]);
       t = 0;
       k = 0;
       if (MODE == MODE_EMIT) obase = offsets[item] - off_base;
@@ -182,8 +235,8 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       target = j0;  // first position: p = Q(j0) / S
       look = true;
     }
-    const int* W = SINGLE ? (const int*)G1.w : w_l;
-    const unsigned long long S = SINGLE ? (unsigned long long)G1.S_i : S_l;
+    const w_t* W = SINGLE ? (const w_t*)G1.w : w_l;
+    const q_t S = SINGLE ? T::S(G1) : S_l;
     // ---- (3) one skip for running items, with the precomputed draw t
     const u32x4 cur = pb;
     if (have && !fresh) {
@@ -192,10 +245,10 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       long long R = (long long)end - (long long)j;
       long long delta = 0;
       if (Qprev != S) {
-        delta = floor_decide_ff(ff_div(pLr, Lp), R);
+        delta = T::skip1(pLr, Lp, R);
         if (delta == SKIP_UNDECIDED) {
           bool tie;
-          delta = skip_fallback_dd(2ull * grid52(cur.x, cur.y) + 1ull, S - Qprev, S, R, &tie);
+          delta = T::skip2(2ull * grid52(cur.x, cur.y) + 1ull, Qprev, S, R, &tie);
           ++n_fb;
           n_tie += tie;
         }
@@ -209,14 +262,13 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
     }
     if (look) {
       // ---- (4) weight of the candidate (or of the first position); meanwhile the next draw
-      const int wt = __ldg(&W[target]);
+      const w_t wt = __ldg(&W[target]);
       pb = philox4x32_10(u32x4{t, seg, u, 0u}, SINGLE ? G1.key0 : k0_l, SINGLE ? G1.key1 : k1_l);
       pLr = ff_neglog_r53(2ull * grid52(pb.x, pb.y) + 1ull);
-      unsigned long long q = (unsigned long long)((long long)wu * (long long)wt);
-      const unsigned long long Qt = q < S ? q : S;
+      const q_t Qt = T::Q(wu, wt, S);
       // ---- (5) acceptance r_a < q / p, with the draw that made the candidate
       if (!fresh) {
-        bool acc = (Qt == Qprev) || accept_i(grid52(cur.z, cur.w), Qprev, Qt);
+        bool acc = (Qt == Qprev) || T::accept(grid52(cur.z, cur.w), Qprev, Qt);
         if (acc) {
           if (MODE == MODE_EMIT) {
             long long pos = obase + k;
@@ -251,7 +303,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         if (Qt == 0)
           done = true;  // p = 0: no further edge
         else if (Qt < S)
-          Lp = ff_neglog1m(Qt, S, SINGLE ? ff{G1.S_ff_hi, G1.S_ff_lo} : ff{Sh_l, Sl_l});
+          Lp = T::Lp(Qt, S, SINGLE ? ff{G1.S_ff_hi, G1.S_ff_lo} : ff{Sh_l, Sl_l});
       }
       j = fresh ? target : target + 1;
       if (j >= end) done = true;
@@ -385,24 +437,34 @@ __global__ void __launch_bounds__(COPY_THREADS) copy_kernel(DevPlan P, long long
 int sampler_max_blocks_per_sm(int block, bool emit, int etype) {
   int nb = 0;
   if (!emit)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_STAGE, false, int2>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_STAGE, false, false, int2>, block, 0);
   else if (etype == CL_E_I32)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_EMIT, false, int2>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_EMIT, false, false, int2>, block, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_EMIT, false, longlong2>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sample_kernel<MODE_EMIT, false, false, longlong2>, block, 0);
   return nb;
+}
+
+template <int MODE, bool WF, typename E>
+static void launch_sampler_w(const DevPlan& P, const DevGraph* single, long long ib, long long ie,
+                             const long long* offsets, E* edges, long long capacity, int* counts, int regen,
+                             int block, int grid, cudaStream_t s) {
+  if (single)
+    sample_kernel<MODE, true, WF, E>
+        <<<grid, block, 0, s>>>(P, *single, ib, ie, offsets, edges, capacity, counts, regen);
+  else
+    sample_kernel<MODE, false, WF, E>
+        <<<grid, block, 0, s>>>(P, DevGraph{}, ib, ie, offsets, edges, capacity, counts, regen);
 }
 
 template <int MODE, typename E>
 static void launch_sampler(const DevPlan& P, const DevGraph* single, long long ib, long long ie,
                            const long long* offsets, E* edges, long long capacity, int* counts, int regen, int block,
                            int grid, cudaStream_t s) {
-  if (single)
-    sample_kernel<MODE, true, E>
-        <<<grid, block, 0, s>>>(P, *single, ib, ie, offsets, edges, capacity, counts, regen);
+  if (P.wf64)
+    launch_sampler_w<MODE, true, E>(P, single, ib, ie, offsets, edges, capacity, counts, regen, block, grid, s);
   else
-    sample_kernel<MODE, false, E>
-        <<<grid, block, 0, s>>>(P, DevGraph{}, ib, ie, offsets, edges, capacity, counts, regen);
+    launch_sampler_w<MODE, false, E>(P, single, ib, ie, offsets, edges, capacity, counts, regen, block, grid, s);
 }
 
 void launch_count(const DevPlan& P, const DevGraph* single, int* d_counts, bool stage, int block, int grid,
