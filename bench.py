@@ -264,6 +264,13 @@ def run_ours(args, rank: int, world: int):
                "d2h_bytes_per_step": 8 * em[-1], "steps": e_steps}
         del out_host, w_host
 
+    # free the main leg's buffers (tens of GB) before the other legs
+    del edges, ws, counts, offsets, w, scratch
+    torch.cuda.empty_cache()
+    batched = None if (args.no_batch or world > 1) else batch_leg(P, dev, args)
+    torch.cuda.empty_cache()
+    calib = None if (args.no_calib or world > 1) else calibrate_leg(dev)
+
     if rank != 0:
         return
     line = {
@@ -280,10 +287,109 @@ def run_ours(args, rank: int, world: int):
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "batched": batched,
+        "calibrate": calib,
     }
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w_np, seed)
     print(json.dumps(line), flush=True)
+
+
+def batch_leg(P, dev, args):
+    """4096 graphs (n log-uniform in [10^3, 10^6], gamma in [2.1, 3.0], degrees on
+    [2, sqrt(n)], seeds 0..4095) in one plan: cl_generate_batch captured in a CUDA
+    graph and replayed, against the same graphs as back-to-back single-graph
+    count/scan/emit launches on one stream; both outputs must be identical."""
+    import torch
+
+    from paper_1406_1215_gb300 import autotune, inputs
+    from paper_1406_1215_gb300.generator import Generator
+
+    work = inputs.batch_workload(args.batch_graphs)
+    sizes = np.array([len(w) for w, _ in work], dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    W = torch.from_numpy(np.concatenate([w for w, _ in work])).to(dev)
+    views = [W[int(offs[i]):int(offs[i + 1])] for i in range(len(work))]
+    seeds = [s for _, s in work]
+    G = len(views)
+    knobs, timings = autotune.tune(views, seeds, reps=1, use_cache=False,
+                                   candidates=[{}, {"block": 128}, {"blocks_per_sm": 2}, {"tasks": 1 << 18}])
+    gen = Generator(views, seeds, **knobs)
+    gen.count()
+    m = gen.scan(True)
+    edges = torch.empty((m + 1024, 2), dtype=torch.int32, device=dev)
+    goff = torch.empty(G + 1, dtype=torch.int64, device=dev)
+    status = torch.empty(1, dtype=torch.int32, device=dev)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        gen.generate_batch(edges, goff, status)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gen.generate_batch(edges, goff, status)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    reps = 5
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        graph.replay()
+    b.record()
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(b) / 1e3 / reps
+    assert int(status.item()) == 0
+    ref = edges[:m].clone()
+    go = goff.cpu().numpy()
+    # back-to-back single-graph launches of the same graphs into the same layout
+    singles = [Generator(v, s, **knobs) for v, s in zip(views, seeds)]
+    out = torch.full_like(edges, -1)
+    slices = [out[int(go[i]):int(go[i + 1])] for i in range(G)]
+
+    def run_singles():
+        for g, sl in zip(singles, slices):
+            P.cl_count(g.plan, g.counts)
+            P.cl_scan(g.plan, g.counts, g.offsets, False)
+            P.cl_emit(g.plan, g.offsets, P.CL_E_I32, sl, sl.shape[0], 0, g.n_items)
+
+    run_singles()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(2):
+        run_singles()
+    b.record()
+    torch.cuda.synchronize()
+    t_single = a.elapsed_time(b) / 1e3 / 2
+    same = bool(torch.equal(out[:m], ref))
+    for g in singles:
+        g.close()
+    gen.close()
+    return {"graphs": G, "edges": int(m), "nodes": int(offs[-1]), "graphs_per_s": G / t_batch,
+            "ms_per_batch": t_batch * 1e3, "single_launch_graphs_per_s": G / t_single,
+            "ms_back_to_back": t_single * 1e3, "speedup_vs_single_launches": t_single / t_batch,
+            "identical_output": same, "cuda_graph": True, "tuning": knobs,
+            "autotune": [{"knobs": r["knobs"], "ms": r["seconds"] * 1e3} for r in timings]}
+
+
+def calibrate_leg(dev):
+    """Weight calibration of n = 10^7 target degrees (gamma 2.1 on [5, 2*10^5])
+    to 1e-9 relative through cl_calibrate."""
+    import torch
+
+    from paper_1406_1215_gb300 import inputs
+    from paper_1406_1215_gb300.calibration import calibrate
+
+    d = torch.from_numpy(inputs.calibration_targets()).to(dev)
+    calibrate(d[:100000].clone(), tol=1e-6)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w, rep = calibrate(d, tol=1e-9)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    return {"seconds": sec, "iterations": rep["iterations"], "max_rel_err": rep["max_rel_err"],
+            "converged": rep["converged"], "n": int(d.numel()), "tol": 1e-9}
 
 
 def main():
@@ -296,6 +402,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="pl_n1e8", choices=sorted(WORKLOADS))
     ap.add_argument("--no-stage", action="store_true", help="count-only first pass; emit regenerates")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 4096-graph batched leg")
+    ap.add_argument("--no-calib", action="store_true", help="skip the calibration leg")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

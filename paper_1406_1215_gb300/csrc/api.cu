@@ -32,6 +32,7 @@ struct cl_plan {
   unsigned long long pool_cap = 0;    // staging pool entries
   bool staged = false;                // the last cl_count staged (cl_emit copies)
   bool tiny_slots = false;            // testing knob: 8-entry slots (most items regenerate)
+  unsigned ovf_cap = 1;               // regeneration list entries
   // workspace (after cl_plan_build)
   bool built = false;
   size_t ws_bytes = 0;
@@ -143,7 +144,7 @@ WsLayout ws_layout(void* base, const cl_plan* p) {
   L.overflow = c.take<int>(4);
   L.slot32 = p->stage ? c.take<int>(p->n_items > 0 ? p->n_items : 1) : nullptr;
   L.slot_base = p->stage ? c.take<long long>(p->n_items + 1) : nullptr;
-  L.ovf_list = p->stage ? c.take<long long>(OVF_CAP) : nullptr;
+  L.ovf_list = p->stage ? c.take<long long>(p->ovf_cap) : nullptr;
   L.ovf_count = c.take<unsigned>(4);
   L.pool = p->stage ? c.take<unsigned>(p->pool_cap > 0 ? p->pool_cap : 1) : nullptr;
   L.bytes = c.off;
@@ -165,7 +166,7 @@ DevPlan dev_plan(const cl_plan* p) {
   P.overflow = p->d_overflow;
   P.ovf_list = p->d_ovf_list;
   P.ovf_count = p->d_ovf_count;
-  P.ovf_cap = OVF_CAP;
+  P.ovf_cap = p->ovf_cap;
   P.wf64 = p->wtype == CL_W_F64 ? 1 : 0;
   return P;
 }
@@ -335,11 +336,12 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
   p->grid_emit32 = p->sms * (bps_e32 > 0 ? bps_e32 : 1);
   p->grid_emit64 = p->sms * (bps_e64 > 0 ? bps_e64 : 1);
   long long warps = (long long)p->grid_count * (p->block / 32);
-  // staging pool: item slots of e_i + 4 sqrt(e_i) + 8 entries (rounded up to 8), e_i the
+  // staging pool: item slots of e_i + 4 sqrt(e_i) + 4 entries (rounded up to 8), e_i the
   // uncapped expected edges of item i, sum_i e_i = (S^2 - sum w^2) / (2 S); by
   // Cauchy-Schwarz sum_i sqrt(e_i) <= sqrt(items * sum_i e_i), so this bounds the pool
   p->stage = !(tuning && tuning->no_stage);
   p->tiny_slots = tuning && tuning->stage_factor < 0;
+  p->ovf_cap = (unsigned)(items < (long long)OVF_CAP ? (items > 0 ? items : 1) : OVF_CAP);
   if (p->stage) {
     double em = 0;
     for (int g = 0; g < G; ++g) {
@@ -347,7 +349,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
       if (S > 0) em += (S * S - res[g].S2) / (2.0 * S);
     }
     if (em < 0) em = 0;
-    double cap = em + 4.0 * std::sqrt((double)items * em) + 16.0 * (double)items + 64.0;
+    double cap = em + 4.0 * std::sqrt((double)items * em) + 12.0 * (double)items + 64.0;
     p->pool_cap = (unsigned long long)cap;
   }
   long long T = (tuning && tuning->tasks > 0) ? tuning->tasks : 16 * warps;

@@ -381,8 +381,8 @@ __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __r
   e = fminf(e, 1e15f);
   C[i] = 16ll + (long long)(16.0f * e + 0.5f);
   if (slot) {
-    // staging slot: e + 4 sd + 8 entries in whole sectors, at most the item's length
-    float want = tiny_slots ? 8.0f : e + 4.0f * sqrtf(e) + 8.0f;
+    // staging slot: e + 4 sd + 4 entries in whole sectors, at most the item's length
+    float want = tiny_slots ? 8.0f : e + 4.0f * sqrtf(e) + 4.0f;
     float len = (float)(end - j0);
     want = fminf(want, len);
     want = fminf(want, 1e9f);

@@ -21,7 +21,7 @@
 //
 // Modes: COUNT writes per-item edge counts; STAGE also writes each item's
 // destinations, in order, into the item's slot of a staging pool (slot sizes
-// come from the plan: expected edges + 4 sd + 8, in whole 32-byte sectors;
+// come from the plan: expected edges + 4 sd + 4, in whole 32-byte sectors;
 // an item that outgrows its slot is regenerated by EMIT).  A lane collects 8
 // entries in shared memory and writes them as one whole sector, since a
 // partially written sector costs a read-modify-write of HBM when evicted;
