@@ -42,7 +42,17 @@ WORKLOADS = {
 COMMON = {"heavy_w": 8192.0, "segment": 65536, "etype": "int32 pairs",
           "l2": "inputs (weights, >= 40 MB) and outputs (>= 1 GB edges) exceed the 129 MB L2 between steps; "
                 "no flush"}
-KERNELS_PER_STEP = 14  # analyze 1 + weight prefix 3 + costs/scan/tasks 5 + count 1 + count scan 3 + emit 1
+# kernels per step: analyze 1, weight prefix 3, costs + cost prefix + task bounds 5, slot prefix 3,
+# count (staged) 1, count scan 3, copy 1, regeneration 1
+KERNELS_PER_STEP = 18
+# ALU roofline of the dominant kernel (the staged count pass): one Philox4x32-10 block per
+# loop iteration is the irreducible arithmetic of the stream; a block needs 20 32x32->64-bit
+# multiplies; an SM issues 32 of them per clock (4 SMSPs x 32 lanes at the half-rate integer
+# multiply, two halves per wide product): 152 SMs x 32 / 20 x 2.07 GHz.
+PHILOX_PEAK = 152 * 32 / 20 * 2.07e9
+# DRAM bytes (read + write) of one staged count launch on this workload, from the one-pass
+# ncu capture summarised in profiles/sample_kernel_stage_pl_n1e8.md; None when stale.
+STAGE_TRAFFIC_BYTES = None
 
 
 def peaks():
@@ -173,6 +183,7 @@ def run_ours(args, rank: int, world: int):
     offsets = torch.empty(n_items + 1, dtype=torch.int64, device=dev)
     P.cl_count(plan, counts, sh)
     m = P.cl_scan(plan, counts, offsets, True, sh)
+    iterations = P.cl_stats(plan, sh)["iterations"]
     P.cl_plan_destroy(plan)
     cap = int(m * 1.0005) + 1024
     edges = torch.empty((cap, 2), dtype=torch.int32, device=dev)
@@ -230,7 +241,8 @@ def run_ours(args, rank: int, world: int):
     t_count = statistics.mean(a.elapsed_time(b) for a, b in kern["count"]) / 1e3
     m_step = ms[-1]
     peak, how = peaks()
-    achieved = 8.0 * m_step / t_emit / 1e9
+    step_s = elapsed / args.steps
+    alu = iterations / t_count
 
     # end to end: weights from pinned host memory, edge list back to pinned host memory
     e2e = None
@@ -279,11 +291,14 @@ def run_ours(args, rank: int, world: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32x2", "data": "synthetic",
         "config": dict(WORKLOADS[args.workload], **COMMON),
         "edges_per_step": m_step,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "sample_kernel<emit,int2>", "peak_source": how,
-                     "algorithmic_bytes": "8 B per edge written (int32 pair)"},
+        "roofline": {"bound": "alu", "achieved": alu, "peak": PHILOX_PEAK, "unit": "Philox blocks/s",
+                     "frac": alu / PHILOX_PEAK, "traffic": STAGE_TRAFFIC_BYTES,
+                     "kernel": "sample_kernel<STAGE> (staged count pass)", "iterations_per_launch": iterations,
+                     "peak_source": "derived from SM count, integer-multiply issue rate and max clock"},
+        "hbm_write_roofline": {"achieved": 8.0 * m_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
+                               "frac": 8.0 * m_step / step_s / 1e9 / peak, "peak_source": how,
+                               "algorithmic_bytes": "8 B per edge (int32 pair) per step"},
         "kernel_ms": {"count": t_count * 1e3, "emit": t_emit * 1e3},
-        "hbm_write_frac_step": 8.0 * m_step / (elapsed / args.steps) / 1e9 / peak,
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": KERNELS_PER_STEP * args.steps,

@@ -88,7 +88,7 @@ typedef struct {
   int32_t blocks_per_sm; /* resident blocks per SM for the persistent sampler grid; 0 = automatic */
   int32_t no_stage;      /* 1: cl_count only counts and cl_emit regenerates every item (smaller
                           * workspace, twice the sampling work); 0: cl_count also stages each
-                          * item's destinations in a slot of e + 4 sqrt(e) + 4 entries (e = the
+                          * item's destinations in a slot of e + 6 sqrt(e) + 6 entries (e = the
                           * item's uncapped expected edges, Eq. 1) and cl_emit copies them;
                           * items that outgrow their slot are regenerated by cl_emit */
   double stage_factor;   /* 0; a negative value shrinks every slot to 8 entries, so that most

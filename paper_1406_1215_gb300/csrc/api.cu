@@ -24,6 +24,7 @@ struct cl_plan {
   long long ntiles = 0;
   long long n_items = 0;
   long long psize = 0;  // sum of (n_g + 1)
+  long long csize = 0;  // sum of ceil(n_g / 4096): uniform-block table entries
   int T = 1;
   int block = 256;
   int grid_count = 0, grid_emit32 = 0, grid_emit64 = 0;
@@ -52,6 +53,7 @@ struct cl_plan {
   int* d_overflow = nullptr;
   long long* d_ovf_list = nullptr;
   unsigned* d_ovf_count = nullptr;
+  unsigned long long* d_blk = nullptr;
 };
 
 namespace {
@@ -122,6 +124,7 @@ struct WsLayout {
   long long* slot_base;
   long long* ovf_list;
   unsigned* ovf_count;
+  unsigned long long* blk;
   unsigned* pool;
   size_t bytes;
 };
@@ -146,6 +149,8 @@ WsLayout ws_layout(void* base, const cl_plan* p) {
   L.slot_base = p->stage ? c.take<long long>(p->n_items + 1) : nullptr;
   L.ovf_list = p->stage ? c.take<long long>(p->ovf_cap) : nullptr;
   L.ovf_count = c.take<unsigned>(4);
+  const bool runs = p->wtype == CL_W_I32;
+  L.blk = runs ? c.take<unsigned long long>(p->csize > 0 ? p->csize : 1) : nullptr;
   L.pool = p->stage ? c.take<unsigned>(p->pool_cap > 0 ? p->pool_cap : 1) : nullptr;
   L.bytes = c.off;
   return L;
@@ -168,6 +173,7 @@ DevPlan dev_plan(const cl_plan* p) {
   P.ovf_count = p->d_ovf_count;
   P.ovf_cap = p->ovf_cap;
   P.wf64 = p->wtype == CL_W_F64 ? 1 : 0;
+  P.blk = p->d_blk;
   return P;
 }
 
@@ -265,7 +271,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
 
   // item space and per-graph status
   cl_status first_bad = CL_OK;
-  long long items = 0, pbase = 0;
+  long long items = 0, pbase = 0, cbase = 0;
   p->tile_begin.assign(G + 1, 0);
   for (int g = 0; g < G; ++g) {
     DevGraph& d = p->dg[g];
@@ -297,6 +303,8 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     if (gs != CL_OK) d.n_items = 0, d.n_heavy = 0;
     d.item_begin = items;
     d.pbase = pbase;
+    d.bbase = cbase;
+    cbase += (n + (1ll << BLK_SHIFT) - 1) >> BLK_SHIFT;
     items += d.n_items;
     pbase += n + 1;
     p->tile_begin[g + 1] = p->tile_begin[g] + (n + 1 + SCAN_TILE_HOST - 1) / SCAN_TILE_HOST;
@@ -316,6 +324,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
   }
   p->n_items = items;
   p->psize = pbase;
+  p->csize = cbase;
   p->ntiles = p->tile_begin[G];
 
   // launch shape (performance knobs only)
@@ -336,7 +345,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
   p->grid_emit32 = p->sms * (bps_e32 > 0 ? bps_e32 : 1);
   p->grid_emit64 = p->sms * (bps_e64 > 0 ? bps_e64 : 1);
   long long warps = (long long)p->grid_count * (p->block / 32);
-  // staging pool: item slots of e_i + 4 sqrt(e_i) + 4 entries (rounded up to 8), e_i the
+  // staging pool: item slots of e_i + 6 sqrt(e_i) + 6 entries (rounded up to 8), e_i the
   // uncapped expected edges of item i, sum_i e_i = (S^2 - sum w^2) / (2 S); by
   // Cauchy-Schwarz sum_i sqrt(e_i) <= sqrt(items * sum_i e_i), so this bounds the pool
   p->stage = !(tuning && tuning->no_stage);
@@ -349,7 +358,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
       if (S > 0) em += (S * S - res[g].S2) / (2.0 * S);
     }
     if (em < 0) em = 0;
-    double cap = em + 4.0 * std::sqrt((double)items * em) + 12.0 * (double)items + 64.0;
+    double cap = em + 6.0 * std::sqrt((double)items * em) + 14.0 * (double)items + 64.0;
     p->pool_cap = (unsigned long long)cap;
   }
   long long T = (tuning && tuning->tasks > 0) ? tuning->tasks : 16 * warps;
@@ -390,6 +399,7 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   p->d_overflow = L.overflow;
   p->d_ovf_list = L.ovf_list;
   p->d_ovf_count = L.ovf_count;
+  p->d_blk = L.blk;
   cl_status st;
   if ((st = cuda_ok(cudaMemcpyAsync(L.graphs, p->dg.data(), sizeof(DevGraph) * p->G, cudaMemcpyHostToDevice, s))))
     return st;
@@ -403,6 +413,7 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   if ((st = cuda_ok(cudaMemsetAsync(L.ovf_count, 0, 4 * sizeof(unsigned), s)))) return st;
   const bool f64 = p->wtype == CL_W_F64;
   launch_weight_prefix(L.graphs, L.tile_begin, p->G, p->ntiles, f64, L.P, L.part, s);
+  if (!f64) launch_blocks(L.graphs, p->G, p->csize, L.blk, s);
   launch_costs_and_tasks(L.graphs, p->G, p->n_items, f64, L.P, L.C, L.part, L.task, p->T, L.slot32,
                          p->tiny_slots ? 1 : 0, s);
   if (p->stage) launch_count_scan(L.slot32, p->n_items, L.slot_base, L.scan_part, s);  // slot bases

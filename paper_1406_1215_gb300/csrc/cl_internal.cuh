@@ -28,6 +28,7 @@ struct DevGraph {
   int wtype;              // cl_wtype
   float S_ff_hi, S_ff_lo; // S as float-float (integer weights)
   float invS_f;           // 1 / S in single precision (costs only)
+  long long bbase;        // offset of this graph's entries in the uniform-block table (integer weights)
 };
 
 // Per-graph results of the analysis kernel (scratch of cl_plan_create).
@@ -90,6 +91,10 @@ __device__ __forceinline__ int graph_of_item(const DevGraph* gs, int G, long lon
 }
 
 // Kernel-facing view of a built plan.
+// uniform-block table of integer-weight plans (see blocks_kernel)
+constexpr int BLK_SHIFT = 12;
+constexpr unsigned long long BLK_MIXED = ~0ull;  // never (w << 32) | end, since w < 2^31
+
 struct DevPlan {
   const DevGraph* graphs;
   int G;
@@ -106,7 +111,21 @@ struct DevPlan {
   unsigned* ovf_count;
   unsigned ovf_cap;
   int wf64;                     // the plan's weights are doubles
+  const unsigned long long* blk;  // integer weights: uniform-block table (BLK_MIXED or (w << 32) | run end)
 };
+
+// Weight of node v of a graph with weights W and uniform-block offset bbase:
+// from the lane's cached run (v < run_end), else from the block table, else
+// (a block holding a change of weight) from W itself.
+__device__ __forceinline__ int block_weight(const DevPlan& P, const int* W, long long bbase, unsigned v,
+                                            unsigned& run_end, int& run_w) {
+  if (v < run_end) return run_w;
+  const unsigned long long e = __ldg(&P.blk[bbase + (v >> BLK_SHIFT)]);
+  if (e == BLK_MIXED) return __ldg(&W[v]);
+  run_w = (int)(unsigned)(e >> 32);
+  run_end = (unsigned)e;
+  return run_w;
+}
 
 // ---- launchers implemented in plan.cu / sample.cu / diag.cu ----
 constexpr int ANALYZE_CHUNK_HOST = 4096;  // weights per analysis block (matches plan.cu)
@@ -121,6 +140,8 @@ size_t f64_bins_bytes(int G);
 // for double weights); graph g's entries start at pbase_g.
 void launch_weight_prefix(const DevGraph* d_graphs, const long long* d_tile_graph_begin, int G, long long ntiles,
                           bool f64, void* d_P, void* d_partials, cudaStream_t s);
+// Run table of integer weights (see plan.cu).
+void launch_blocks(const DevGraph* d_graphs, int G, long long nblk, unsigned long long* d_blk, cudaStream_t s);
 // Item costs (fixed point, 1/16 edge), their exact inclusive prefix C in place and the
 // task boundaries of Eq. 3; when d_slot32 is given, also every item's staging slot size.
 void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, bool f64, const void* d_P,

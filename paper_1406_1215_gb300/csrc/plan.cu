@@ -358,6 +358,49 @@ void launch_weight_prefix(const DevGraph* d_graphs, const long long* d_tile_grap
   }
 }
 
+// --------------------------------------------------------------- weight blocks
+// Integer weights sorted non-increasing: node block b of graph g (nodes
+// 4096 b .. 4096 b + 4095) is uniform iff its first and last weights are equal.
+// blk[bbase_g + b] = (w << 32) | end for a uniform block, end being the first
+// node after the block's run (found by bisection over the sorted weights), and
+// BLK_MIXED for a block that holds a change of weight.  The sampler reads a
+// candidate's weight from this table when its block is uniform (the tail of a
+// power law, where the weight array is far larger than L2) and from the weight
+// array otherwise (the head, a few MB that stay in L2).
+__global__ void __launch_bounds__(PLAN_THREADS) blocks_kernel(const DevGraph* __restrict__ gs, int G,
+                                                              long long nblk, unsigned long long* __restrict__ blk) {
+  const long long x = blockIdx.x * (long long)PLAN_THREADS + threadIdx.x;
+  if (x >= nblk) return;
+  int lo = 0, hi = G - 1;  // last graph with bbase <= x
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (gs[mid].bbase <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  const DevGraph& g = gs[lo];
+  const int* w = (const int*)g.w;
+  const long long n = g.n, a = (x - g.bbase) << BLK_SHIFT;
+  long long last = a + (1ll << BLK_SHIFT) - 1;
+  if (last > n - 1) last = n - 1;
+  const int wa = w[a];
+  if (w[last] != wa) {
+    blk[x] = BLK_MIXED;
+    return;
+  }
+  long long l = last, h = n;  // first index > last with w < wa, in (last, n]
+  while (h - l > 1) {
+    long long mid = (l + h) >> 1;
+    if (w[mid] == wa) l = mid;
+    else h = mid;
+  }
+  blk[x] = ((unsigned long long)(unsigned)wa << 32) | (unsigned long long)h;
+}
+
+void launch_blocks(const DevGraph* d_graphs, int G, long long nblk, unsigned long long* d_blk, cudaStream_t s) {
+  if (nblk <= 0) return;
+  blocks_kernel<<<(unsigned)((nblk + PLAN_THREADS - 1) / PLAN_THREADS), PLAN_THREADS, 0, s>>>(d_graphs, G, nblk, d_blk);
+}
+
 // --------------------------------------------------------------- costs, Eq. 3
 // c_i = 1 + (w_u / S) * sum_{v in [j0, end)} w_v  (Eq. 1-2; for a light row
 // [u+1, n) this is Eq. 6: (w_u / S)(S - sigma_u - w_u) + 1), in fixed point
@@ -381,8 +424,8 @@ __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __r
   e = fminf(e, 1e15f);
   C[i] = 16ll + (long long)(16.0f * e + 0.5f);
   if (slot) {
-    // staging slot: e + 4 sd + 4 entries in whole sectors, at most the item's length
-    float want = tiny_slots ? 8.0f : e + 4.0f * sqrtf(e) + 4.0f;
+    // staging slot: e + 6 sd + 6 entries in whole sectors, at most the item's length
+    float want = tiny_slots ? 8.0f : e + 6.0f * sqrtf(e) + 6.0f;
     float len = (float)(end - j0);
     want = fminf(want, len);
     want = fminf(want, 1e9f);

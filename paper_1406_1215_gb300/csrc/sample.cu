@@ -21,7 +21,7 @@
 //
 // Modes: COUNT writes per-item edge counts; STAGE also writes each item's
 // destinations, in order, into the item's slot of a staging pool (slot sizes
-// come from the plan: expected edges + 4 sd + 4, in whole 32-byte sectors;
+// come from the plan: expected edges + 6 sd + 6, in whole 32-byte sectors;
 // an item that outgrows its slot is regenerated by EMIT).  A lane collects 8
 // entries in shared memory and writes them as one whole sector, since a
 // partially written sector costs a read-modify-write of HBM when evicted;
@@ -145,7 +145,11 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   w_t wu = 0;
   u32x4 pb{0u, 0u, 0u, 0u};  // the lane's next draw (index t) ...
   ff pLr{0.f, 0.f};          // ... and its -ln r_s
+  // the lane's current weight run (integer weights): candidates before run_end weigh run_w
+  unsigned run_end = 0;
+  int run_w = 0;
   // graph of the lane's item (batched plans only)
+  int gi_l = 0;
   const w_t* w_l = nullptr;
   q_t S_l = 0;
   float Sh_l = 0.f, Sl_l = 0.f;
@@ -215,6 +219,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         item_bounds(G1, item, u, seg, j0, end);
       } else {
         int gi = graph_of_item(P.graphs, P.G, item);
+        gi_l = gi;
         const DevGraph& g = P.graphs[gi];
         item_bounds(g, item - g.item_begin, u, seg, j0, end);
         w_l = (const w_t*)g.w;
@@ -225,6 +230,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         k1_l = g.key1;
       }
       wu = __ldg(&(SINGLE ? (const w_t*)G1.w : w_l)[u]);
+      run_end = 0;  // no cached run for the new item
       t = 0;
       k = 0;
       if (MODE == MODE_EMIT) obase = offsets[item] - off_base;
@@ -262,7 +268,13 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
     }
     if (look) {
       // ---- (4) weight of the candidate (or of the first position); meanwhile the next draw
-      const w_t wt = __ldg(&W[target]);
+      w_t wt;
+      if (WF) {
+        wt = __ldg(&W[target]);
+      } else {  // integer weights: uniform-block table, the lane's current run as a cache
+        const long long bbase = SINGLE ? G1.bbase : P.graphs[gi_l].bbase;
+        wt = (w_t)block_weight(P, (const int*)W, bbase, target, run_end, run_w);
+      }
       pb = philox4x32_10(u32x4{t, seg, u, 0u}, SINGLE ? G1.key0 : k0_l, SINGLE ? G1.key1 : k1_l);
       pLr = ff_neglog_r53(2ull * grid52(pb.x, pb.y) + 1ull);
       const q_t Qt = T::Q(wu, wt, S);
