@@ -12,6 +12,22 @@ constexpr int SEG_LOG2 = 16;  // heavy rows are cut at absolute multiples of 2^1
 constexpr unsigned LIGHT_SEG = 0xFFFFFFFFu;
 constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
 
+// Per-graph constants of -ln(1 - Q/S): zS = clz(S), sh = max(0, 41 - zS)
+// (so S >> sh has at most 23 bits) and cS = 64 / (S >> sh) in float.
+struct LpConst {
+  int zS, sh;
+  float cS;
+};
+__host__ __device__ inline LpConst lp_const(unsigned long long S) {
+#ifdef __CUDA_ARCH__
+  const int z = __clzll(S);
+#else
+  const int z = S ? __builtin_clzll(S) : 64;
+#endif
+  const int sh = z < 41 ? 41 - z : 0;
+  return LpConst{z, sh, (float)(64.0 / (double)(S >> sh))};
+}
+
 // One graph of a plan, as the kernels see it (lives in the plan workspace).
 struct DevGraph {
   const void* w;          // device weights, sorted non-increasing
@@ -26,7 +42,8 @@ struct DevGraph {
   long long n_items;      // items of this graph
   long long pbase;        // offset of this graph's weight prefix (n + 1 entries)
   int wtype;              // cl_wtype
-  float S_ff_hi, S_ff_lo; // S as float-float (integer weights)
+  int lp_zS, lp_sh;       // constants of -ln(1 - Q/S) (integer weights, see lp_const)
+  float lp_cS;
   float invS_f;           // 1 / S in single precision (costs only)
   long long bbase;        // offset of this graph's entries in the uniform-block table (integer weights)
 };
@@ -51,16 +68,16 @@ __host__ __device__ __forceinline__ long long heavy_items_before(long long U, lo
   return U * (N1 + 1) - F;
 }
 
-// Bounds of a graph's local item: source row u, segment field, [j0, end).
-__device__ __forceinline__ void item_bounds(const DevGraph& g, long long local, unsigned& u, unsigned& seg,
-                                            unsigned& j0, unsigned& end) {
-  if (local >= g.n_heavy) {
-    u = (unsigned)(g.H + (local - g.n_heavy));
-    seg = LIGHT_SEG;
-    j0 = u + 1;
-    end = (unsigned)g.n;
-    return;
-  }
+// Position of a graph's local item: source row u and segment field (LIGHT_SEG
+// for a light row).  Heavy row u has the segments (u + 1) >> 16 .. N1.
+struct ItemPos {
+  long long local;
+  unsigned u, seg;
+};
+
+// By bisection over the heavy rows (for an item with no known neighbour).
+__device__ __forceinline__ ItemPos item_pos(const DevGraph& g, long long local) {
+  if (local >= g.n_heavy) return ItemPos{local, (unsigned)(g.H + (local - g.n_heavy)), LIGHT_SEG};
   long long lo = 0, hi = g.Hh - 1;  // last r with heavy_items_before(r) <= local
   while (lo < hi) {
     long long mid = (lo + hi + 1) >> 1;
@@ -69,12 +86,57 @@ __device__ __forceinline__ void item_bounds(const DevGraph& g, long long local, 
     else
       hi = mid - 1;
   }
-  long long k = ((lo + 1) >> SEG_LOG2) + (local - heavy_items_before(lo, g.n));
-  long long s0 = k << SEG_LOG2, s1 = (k + 1) << SEG_LOG2;
-  u = (unsigned)lo;
-  seg = (unsigned)k;
-  j0 = (unsigned)(s0 > lo + 1 ? s0 : lo + 1);
+  const long long k = ((lo + 1) >> SEG_LOG2) + (local - heavy_items_before(lo, g.n));
+  return ItemPos{local, (unsigned)lo, (unsigned)k};
+}
+
+// The position d >= 0 items after p (p.local + d an item of g): segments
+// advance within the row, and a step past the row's last segment moves to the
+// first segment of the next row -- one loop turn per row crossed.
+__device__ __forceinline__ ItemPos item_advance(const DevGraph& g, ItemPos p, long long d) {
+  const long long t = p.local + d;
+  if (t >= g.n_heavy) return ItemPos{t, (unsigned)(g.H + (t - g.n_heavy)), LIGHT_SEG};
+  const long long N1 = (g.n - 1) >> SEG_LOG2;
+  unsigned u = p.u;
+  long long k = (long long)p.seg + d;
+  while (k > N1) {
+    k -= N1 + 1;
+    ++u;
+    k += (long long)((u + 1) >> SEG_LOG2);
+  }
+  return ItemPos{t, u, (unsigned)k};
+}
+
+// Candidate range [j0, end) of the item at p.
+__device__ __forceinline__ void pos_bounds(const DevGraph& g, ItemPos p, unsigned& j0, unsigned& end) {
+  if (p.seg == LIGHT_SEG) {
+    j0 = p.u + 1;
+    end = (unsigned)g.n;
+    return;
+  }
+  const long long s0 = (long long)p.seg << SEG_LOG2, s1 = s0 + (1ll << SEG_LOG2);
+  j0 = (unsigned)(s0 > (long long)p.u + 1 ? s0 : (long long)p.u + 1);
   end = (unsigned)(s1 < g.n ? s1 : g.n);
+}
+
+// Bounds of a graph's local item: source row u, segment field, [j0, end).
+__device__ __forceinline__ void item_bounds(const DevGraph& g, long long local, unsigned& u, unsigned& seg,
+                                            unsigned& j0, unsigned& end) {
+  const ItemPos p = item_pos(g, local);
+  u = p.u;
+  seg = p.seg;
+  pos_bounds(g, p, j0, end);
+}
+
+// Walk a cursor (graph gi, position p of the global item it stands on) d items
+// forward across graph boundaries; the result must be an item of the plan.
+__device__ __forceinline__ void cursor_advance(const DevGraph* gs, int& gi, ItemPos& p, long long d) {
+  while (p.local + d >= gs[gi].n_items) {  // past this graph: continue at local 0 of the next
+    d -= gs[gi].n_items - p.local;
+    ++gi;
+    p = gs[gi].n_heavy > 0 ? ItemPos{0, 0u, 0u} : ItemPos{0, (unsigned)gs[gi].H, LIGHT_SEG};
+  }
+  p = item_advance(gs[gi], p, d);
 }
 
 // Graph owning a global item (binary search over item_begin; G is small).

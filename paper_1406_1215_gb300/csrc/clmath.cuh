@@ -15,10 +15,14 @@
 // Both logarithms are of a ratio of integers, -ln(A/B) with 1 <= A < B,
 // computed by table-driven argument reduction (Tang, ACM TOMS 15(2), 1989/90)
 // and the atanh series:
-//   A' = A 2^e in [B/2, B);  J = round(64 A'/B) in [32, 64];
+//   A' = A 2^e near B;  J = round(64 A'/B);
 //   -ln(A/B) = e ln2 + ln(64/J) - 2 atanh(s),  s = (64A' - JB) / (64A' + JB),
 // where s is formed from exact integers, so no cancellation is lost for
-// p -> 0 (A -> B) or p -> 1 (A -> 0).  |s| <= ~1/127.
+// p -> 0 (A -> B) or p -> 1 (A -> 0), and |s| <= ~1/127.  The float-float
+// tier evaluates both logarithms of a skip on one branch-free path (a warp's
+// lanes hold very different p, and a branch on p's size would run both sides
+// for the whole warp); the table has 97 entries, ~800 bytes, so a warp's
+// divergent lookups touch few L1 lines.
 //
 // Float-float and double-double arithmetic follow Dekker (1971) and Knuth
 // (TAOCP vol. 2, 4.2.2): error-free TwoSum, TwoProd via fused multiply-add.
@@ -75,35 +79,49 @@ __device__ __forceinline__ ff ff_mul_f(ff x, float y) {
   p.lo = fmaf(x.lo, y, p.lo);
   return ff_fast_two_sum(p.hi, p.lo);
 }
-// x / y: first quotient from the rounded reciprocal, one correction from the
-// residual x - q1 y (q1 * y.hi is exact as a TwoProd; x.hi - p.hi is exact by
-// Sterbenz' lemma since q1 y.hi is within a few ulps of x.hi).
+// 1/y for a normal float y > 0: the hardware approximation (rcp.approx, at
+// most one ulp off) refined by one Newton-Raphson step r + r (1 - y r), which
+// leaves it within about one ulp of 1/y at the cost of two FMAs.
+__device__ __forceinline__ float rcp_nr(float y) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return fmaf(r, fmaf(-y, r, 1.0f), r);
+}
+// x / y (y > 0): first quotient q1 = x.hi / y.hi from the reciprocal; the
+// residual x - q1 y formed with FMAs (x.hi - q1 y.hi is rounded once, at
+// ~2^-23 |x|), second quotient from it.  Relative error below ~2^-44.
 __device__ __forceinline__ ff ff_div(ff x, ff y) {
-  float r = __frcp_rn(y.hi);
-  float q1 = __fmul_rn(x.hi, r);
-  ff p = ff_two_prod(q1, y.hi);
-  float e = __fsub_rn(x.hi, p.hi);
-  e = __fsub_rn(e, p.lo);
+  const float r = rcp_nr(y.hi);
+  const float q1 = __fmul_rn(x.hi, r);
+  float e = fmaf(-q1, y.hi, x.hi);
   e = __fadd_rn(e, x.lo);
   e = fmaf(-q1, y.lo, e);
-  float q2 = __fmul_rn(e, r);
-  return ff_fast_two_sum(q1, q2);
+  return ff_fast_two_sum(q1, __fmul_rn(e, r));
 }
 // ---- integer -> float without conversion instructions.  On this GPU the
 // int<->float conversion instructions share the slow FP64-class pipe, so the
-// per-candidate path builds floats from integer bits instead: for
-// 0 <= x < 2^23 the float with biased exponent 150 and significand bits x is
-// exactly 2^23 + x.
+// per-candidate path builds floats from integer bits instead: the float with
+// biased exponent 150 + k and significand bits x (0 <= x < 2^23) is exactly
+// 2^(23+k) + x 2^k, so subtracting 2^(23+k) leaves x 2^k exactly.  For
+// u23_to_f (exponent field 150, its lowest bit clear) x = 2^23 works too: the
+// or-ed bit lands in the exponent and gives 2^24.
 __device__ __forceinline__ float u23_to_f(unsigned x) {
   return __fsub_rn(__int_as_float(0x4B000000u | x), 8388608.0f);
 }
-// unsigned 64-bit integer to float-float: three exact 23-bit chunks, summed
-// with one error-free TwoSum; exact below 2^46, relative error < 2^-47 above.
+__device__ __forceinline__ float u23_to_f_2p23(unsigned x) {  // x 2^23
+  return __fsub_rn(__int_as_float(0x56800000u | x), 0x1p46f);
+}
+__device__ __forceinline__ float u23_to_f_2p46(unsigned x) {  // x 2^46
+  return __fsub_rn(__int_as_float(0x62000000u | x), 0x1p69f);
+}
+// unsigned 64-bit integer to float-float from three exact 23-bit chunks: the
+// top two sum exactly (FastTwoSum, the larger first), the third is added with
+// one rounding.  Exact below 2^46; relative error below 2^-46.4 above.
 __device__ __forceinline__ ff ff_from_u64(unsigned long long x) {
-  float f2 = __fmul_rn(u23_to_f((unsigned)(x >> 46)), 0x1p46f);
-  float f1 = __fmul_rn(u23_to_f((unsigned)(x >> 23) & 0x7FFFFFu), 0x1p23f);
-  float f0 = u23_to_f((unsigned)x & 0x7FFFFFu);
-  ff s = ff_two_sum(f2, f1);
+  const float f2 = u23_to_f_2p46((unsigned)(x >> 46));
+  const float f1 = u23_to_f_2p23((unsigned)(x >> 23) & 0x7FFFFFu);
+  const float f0 = u23_to_f((unsigned)x & 0x7FFFFFu);
+  ff s = ff_fast_two_sum(f2, f1);
   s.lo = __fadd_rn(s.lo, f0);
   return ff_fast_two_sum(s.hi, s.lo);
 }
@@ -111,70 +129,78 @@ __device__ __forceinline__ ff ff_from_i64(long long v) {
   ff r = ff_from_u64((unsigned long long)(v < 0 ? -v : v));
   return v < 0 ? ff{-r.hi, -r.lo} : r;
 }
+// |v| <= 2^46, exactly: two 23-bit chunks.
+__device__ __forceinline__ ff ff_from_i47(long long v) {
+  const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+  ff r = ff_fast_two_sum(__fmul_rn(u23_to_f((unsigned)(a >> 23)), 0x1p23f), u23_to_f((unsigned)a & 0x7FFFFFu));
+  return v < 0 ? ff{-r.hi, -r.lo} : r;
+}
 
-// 2 atanh(s) and the table/exponent terms shared by the two reductions:
-// returns e ln2 + ln(64/J) - 2 atanh(s).
-__device__ __forceinline__ ff ff_reduce_tail(ff s, int e, int J) {
-  // atanh(s) = s (1 + z (1/3 + z/5 + z^2/7 + z^3/9)), z = s^2, |s| <~ 2^-7
-  ff z = ff_two_prod(s.hi, s.hi);
-  z.lo = fmaf(2.0f * s.hi, s.lo, z.lo);
-  z = ff_fast_two_sum(z.hi, z.lo);
-  float tail = z.hi * fmaf(z.hi, fmaf(z.hi, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f);
-  // 1/3 + tail: tail < 2^-14, its float rounding is far below the target
-  ff P2 = ff_fast_two_sum(CL_THIRD_FF_HI, __fadd_rn(tail, CL_THIRD_FF_LO));
-  ff c = ff_mul(z, P2);        // z (1/3 + ...)
-  ff sc = ff_mul(s, c);        // s z (...), |sc| < 2^-14 |s|
-  ff at = ff_add_fast(s, sc);  // atanh(s)
-  ff t = ff{__ldg(&CL_LNT_FF[J - 32][0]), __ldg(&CL_LNT_FF[J - 32][1])};
-  ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f((unsigned)e));
-  ff r = ff_add_fast(le, t);  // both >= 0
-  // r - 2 atanh(s) >= (r + |2 atanh(s)|) / 4 (|2 atanh s| <~ r for J < 64; r = 0 for J = 64)
+// e ln2 + ln(64/J) - 2 atanh(s) for |s| <= 1/127, J in [32, 128], e >= 1 when
+// J > 64 (then written (e - 1) ln2 + ln(128/J), so both leading terms are
+// non-negative and are added without cancellation; with |2 atanh s| at most
+// about half of ln(64/J) or ln(128/J) for J != 64, 128, the last sum loses at
+// most one bit).
+//   atanh(s) = s + s m,  m = z (1/3 + z/5 + z^2/7),  z = s^2,
+// dropped terms below 2^-59 |s|; |m| < 2^-15.6, so m is needed to ~2^-32 only:
+// z/3 as a pair (exact product error, the lo parts of z and 1/3), the rest in
+// float.
+__device__ __forceinline__ ff ff_log_tail(ff s, int e, int J) {
+  const float z = __fmul_rn(s.hi, s.hi);
+  const float zl = fmaf(2.0f * s.hi, s.lo, fmaf(s.hi, s.hi, -z));
+  const float tail = __fmul_rn(z, fmaf(z, 1.0f / 7.0f, 1.0f / 5.0f));
+  const float mh = __fmul_rn(z, CL_THIRD_FF_HI);
+  float ml = fmaf(z, CL_THIRD_FF_HI, -mh);
+  ml = fmaf(z, __fadd_rn(CL_THIRD_FF_LO, tail), ml);
+  ml = fmaf(zl, CL_THIRD_FF_HI, ml);
+  const float ch = __fmul_rn(s.hi, mh);
+  float cl = fmaf(s.hi, mh, -ch);
+  cl = fmaf(s.hi, ml, cl);
+  cl = fmaf(s.lo, mh, cl);
+  ff at = ff_fast_two_sum(s.hi, ch);  // |ch| < 2^-15 |s.hi|
+  at.lo = __fadd_rn(at.lo, __fadd_rn(s.lo, cl));
+  const float2 t = __ldg(&CL_LNT2_FF[J - 32]);
+  const unsigned e2 = (unsigned)(e - (J > 64 ? 1 : 0));
+  const ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f(e2));
+  const ff r = ff_add_fast(le, ff{t.x, t.y});
   return ff_add_fast(r, ff{-2.0f * at.hi, -2.0f * at.lo});
 }
 
-// -ln(A / B) for integers 1 <= A < B <= 2^55, as float-float.
-__device__ __forceinline__ ff ff_neglog_ratio(unsigned long long A, unsigned long long B) {
-  int e = __clzll(A) - __clzll(B);
-  unsigned long long Ap = A << e;
-  if (Ap >= B) {
-    Ap >>= 1;
-    e -= 1;
-  }
-  // J = round(64 A'/B) from the top 23 bits (an off-by-one J only widens |s| slightly)
-  int sh = 41 - __clzll(B);
-  sh = sh < 0 ? 0 : sh;
-  float q = 64.0f * u23_to_f((unsigned)(Ap >> sh)) * __frcp_rn(u23_to_f((unsigned)(B >> sh)));
-  int J = __float_as_int(__fadd_rn(q, 12582912.0f)) - 0x4B400000;  // round to nearest
-  J = J < 32 ? 32 : (J > 64 ? 64 : J);
-  long long N = (long long)(Ap << 6) - (long long)J * (long long)B;
-  long long D = (long long)(Ap << 6) + (long long)J * (long long)B;
-  return ff_reduce_tail(ff_div(ff_from_i64(N), ff_from_u64((unsigned long long)D)), e, J);
-}
-
-// -ln r for r = A / 2^53, A odd in [1, 2^53): the reduction needs no division
-// to pick J (B is a power of two) and s = N / (J 2^48 + N), N = A' - J 2^47.
+// -ln r for r = A / 2^53, A odd in [1, 2^53) (Tang's reduction with a
+// power-of-two denominator): A' = A 2^e in [2^52, 2^53), J = round(A' / 2^47)
+// in [32, 64], N = A' - J 2^47 in [-2^46, 2^46) (exact as float-float),
+//   -ln r = e ln2 + ln(64/J) - 2 atanh(s),  s = N / (J 2^48 + N).
 __device__ __forceinline__ ff ff_neglog_r53(unsigned long long A) {
-  int e = __clzll(A) - 11;
-  unsigned long long Ap = A << e;                      // [2^52, 2^53)
-  int J = (int)((Ap + (1ull << 46)) >> 47);            // [32, 64]
-  long long N = (long long)Ap - ((long long)J << 47);  // [-2^46, 2^46]
-  ff Nf = ff_from_i64(N);
-  ff Df = ff_add_fast(ff{__fmul_rn(u23_to_f((unsigned)J), 0x1p48f), 0.0f}, Nf);  // |N| <= J 2^48 / 64
-  return ff_reduce_tail(ff_div(Nf, Df), e, J);
+  const int e = __clzll(A) - 11;
+  const unsigned long long Ap = A << e;
+  const int J = (int)((Ap + (1ull << 46)) >> 47);
+  const long long N = (long long)Ap - ((long long)J << 47);
+  const ff Nf = ff_from_i47(N);
+  // J 2^48 + N: the first sum is exact (|N| < 2^46 < J 2^48), the second rounds
+  // once, below 2^-47 of the total
+  ff Df = ff_fast_two_sum(__fmul_rn(u23_to_f((unsigned)J), 0x1p48f), Nf.hi);
+  Df.lo = __fadd_rn(Df.lo, Nf.lo);
+  return ff_log_tail(ff_div(Nf, Df), e, J);
 }
 
-// -ln(1 - Q/S) for integers 0 < Q < S <= 2^48.  For p = Q/S < 2^-12 the series
-// p (1 + p/2 + p^2/3 + p^3/4 + p^4/5) (next term < 2^-50 relative); otherwise
-// the table reduction of -ln((S - Q) / S).
-__device__ __forceinline__ ff ff_neglog1m(unsigned long long Q, unsigned long long S, ff Sf) {
-  if (Q < (S >> 12)) {
-    ff p = ff_div(ff_from_u64(Q), Sf);
-    float t = p.hi * p.hi * fmaf(p.hi, fmaf(p.hi, 0.2f, 0.25f), 1.0f / 3.0f);
-    ff c = ff_fast_two_sum(1.0f, 0.5f * p.hi);
-    c.lo = __fadd_rn(c.lo, __fadd_rn(0.5f * p.lo, t));
-    return ff_mul(p, c);
-  }
-  return ff_neglog_ratio(S - Q, S);
+// -ln(1 - Q/S) = -ln(A/S), A = S - Q, for integers 0 < Q < S < 2^53; one path
+// for every p (no branch on its size, so lanes of a warp stay converged):
+//   A' = A 2^e with S's leading bit, A'/S in (1/2, 2);  J = round(64 A'/S)
+//   in [32, 128] (from 23-bit leading parts, off by at most 2^-13.7 before
+//   rounding);  N = 64 A' - J S, D = 64 A' + J S exactly in 64-bit integers;
+//   -ln(A/S) = e ln2 + ln(64/J) - 2 atanh(N/D).
+// For p < 1/2048 this is e = 0, J = 64, N = -64 Q: the pure atanh series,
+// with full relative precision however small p is.
+__device__ __forceinline__ ff ff_neglog1m(unsigned long long Q, unsigned long long S, LpConst c) {
+  const unsigned long long A = S - Q;
+  const int e = __clzll(A) - c.zS;
+  const unsigned long long Ap = A << e;
+  const float q = __fmul_rn(u23_to_f((unsigned)(Ap >> c.sh)), c.cS);
+  int J = __float_as_int(__fadd_rn(q, 12582912.0f)) - 0x4B400000;  // round to nearest
+  J = J < 32 ? 32 : (J > 128 ? 128 : J);
+  const unsigned long long JS = (unsigned long long)(unsigned)J * S;
+  const unsigned long long A64 = Ap << 6;
+  return ff_log_tail(ff_div(ff_from_i64((long long)(A64 - JS)), ff_from_u64(A64 + JS)), e, J);
 }
 
 // ------------------------------------------------------------- double-double

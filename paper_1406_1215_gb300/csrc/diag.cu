@@ -45,7 +45,7 @@ __global__ void diag_neglog_kernel(const unsigned long long* __restrict__ A, con
     return;
   }
   // the float-float forms the sampler uses: -ln r (B = 2^53) or -ln(1 - Q/S)
-  ff f = B[i] == (1ull << 53) ? ff_neglog_r53(A[i]) : ff_neglog1m(B[i] - A[i], B[i], ff_from_u64(B[i]));
+  ff f = B[i] == (1ull << 53) ? ff_neglog_r53(A[i]) : ff_neglog1m(B[i] - A[i], B[i], lp_const(B[i]));
   dd d = dd_neglog_ratio(A[i], B[i]);
   oft[2 * i] = f.hi;
   oft[2 * i + 1] = f.lo;
@@ -66,7 +66,7 @@ __global__ void diag_skip_kernel(const unsigned long long* __restrict__ a, const
   }
   unsigned long long Ar = 2ull * a[i] + 1ull;
   ff Lr = ff_neglog_r53(Ar);
-  ff Lp = ff_neglog1m(Q[i], S[i], ff_from_u64(S[i]));
+  ff Lp = ff_neglog1m(Q[i], S[i], lp_const(S[i]));
   long long d = floor_decide_ff(ff_div(Lr, Lp), R[i]);
   int tr = 0;
   if (d == SKIP_UNDECIDED) {

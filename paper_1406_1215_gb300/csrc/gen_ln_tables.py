@@ -1,5 +1,6 @@
-"""Writes ln_tables.h: ln(64/J) for J = 32..64 and the atanh-series
-coefficients 1/(2k+1), split into float-float and double-double pairs.
+"""Writes ln_tables.h: the reduction tables of the logarithms (ln(64/J) for
+J = 32..64, and for J = 65..128 ln(128/J)) and the atanh-series coefficients
+1/(2k+1), split into float-float and double-double pairs.
 
 Values come from Python's decimal module at 80 significant digits (its ln is
 correctly rounded), so each split is exact to the precision of the pair.
@@ -52,16 +53,19 @@ def split_dd(x: D):
 def main():
     lines = [
         "// Generated by gen_ln_tables.py -- do not edit.",
-        "// T[J - 32] = ln(64 / J), J = 32..64, as float-float and double-double pairs;",
+        "// CL_LNT2_FF[J - 32] = ln(64 / J) for J = 32..64 and ln(128 / J) for",
+        "// J = 65..128 (never negative), as float-float pairs (one 8-byte load);",
+        "// CL_LNT_DD[J - 32] = ln(64 / J), J = 32..64, as double-double pairs;",
         "// ATANH_DD[k] = 1 / (2k + 1) as double-double pairs, k = 0..9.",
         "// Global (not constant) memory: lanes index the table divergently, which",
         "// the constant cache would serialise; reads go through L1.",
         "#pragma once",
         "",
-        "static __device__ float CL_LNT_FF[33][2] = {",
+        "static __device__ __align__(8) float2 CL_LNT2_FF[97] = {",
     ]
-    for J in range(32, 65):
-        hi, lo = split_ff((D(64) / D(J)).ln())
+    for J in range(32, 129):
+        num = 64 if J <= 64 else 128
+        hi, lo = split_ff((D(num) / D(J)).ln())
         lines.append(f"  {{{hexf(hi)}f, {hexf(lo)}f}},  // J = {J}")
     lines.append("};")
     lines.append("static __device__ double CL_LNT_DD[33][2] = {")

@@ -72,7 +72,7 @@ struct Wt<false> {
     q_t q = (q_t)((long long)a * (long long)b);
     return q < S ? q : S;
   }
-  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, ff Sf) { return ff_neglog1m(Q, S, Sf); }
+  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, LpConst c) { return ff_neglog1m(Q, S, c); }
   static __device__ __forceinline__ long long skip1(ff Lr, lp_t Lp, long long R) {
     return floor_decide_ff(ff_div(Lr, Lp), R);
   }
@@ -93,7 +93,7 @@ struct Wt<true> {
     q_t q = a * b;
     return q >= S ? S : q;  // capped iff the rounded product reaches S
   }
-  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, ff) { return d_neglog1m(Q, S); }
+  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, LpConst) { return d_neglog1m(Q, S); }
   static __device__ __forceinline__ long long skip1(ff Lr, lp_t Lp, long long R) {
     return floor_decide_d(((double)Lr.hi + (double)Lr.lo) / Lp, R);
   }
@@ -133,9 +133,11 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       return;  // nothing is written when the range does not fit
     }
   }
-  // warp-uniform task cursor
+  // warp-uniform task cursor: the next item of the task, its graph and position
   long long next = 0, tend = 0;
   bool tasks_left = true;
+  int cg = 0;
+  ItemPos cpos{0, 0u, 0u};
   // lane state
   bool have = false, fresh = false;
   long long item = 0, obase = 0;
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   int gi_l = 0;
   const w_t* w_l = nullptr;
   q_t S_l = 0;
-  float Sh_l = 0.f, Sl_l = 0.f;
+  LpConst lc_l{0, 0, 0.f};
   unsigned k0_l = 0, k1_l = 0;
   unsigned long long sbase = 0;  // staging: the item's slot and its size
   unsigned ssize = 0;
@@ -184,6 +186,11 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         long long a = P.task_start[tix], b = P.task_start[tix + 1];
         next = a > ib ? a : ib;
         tend = b < ie ? b : ie;
+        if (next < tend) {  // position of the task's first item (once per task, warp-uniform)
+          cg = SINGLE ? 0 : graph_of_item(P.graphs, P.G, next);
+          const DevGraph& g = SINGLE ? G1 : P.graphs[cg];
+          cpos = item_pos(g, next - g.item_begin);
+        }
         continue;
       }
       long long avail = tend - next;
@@ -192,17 +199,39 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       if (!have && rank < avail) {
         have = true;
         fresh = true;
-        if (MODE == MODE_EMIT && list_mode) {
+        ItemPos ip{0, 0u, 0u};
+        if (MODE == MODE_EMIT && list_mode) {  // scattered items: locate each by bisection
           item = P.ovf_list[next + rank];
-          if (item < ib || item >= ie) have = fresh = false;
-        } else {
+          if (item < ib || item >= ie) {
+            have = fresh = false;
+          } else {
+            gi_l = SINGLE ? 0 : graph_of_item(P.graphs, P.G, item);
+            const DevGraph& g = SINGLE ? G1 : P.graphs[gi_l];
+            ip = item_pos(g, item - g.item_begin);
+          }
+        } else {  // consecutive items: a few steps from the warp's cursor
           item = next + rank;
+          ip = cpos;
+          gi_l = cg;
+          if (SINGLE)
+            ip = item_advance(G1, ip, rank);
+          else
+            cursor_advance(P.graphs, gi_l, ip, rank);
           if (MODE == MODE_EMIT && regen_only &&
               offsets[item + 1] - offsets[item] <= P.slot_base[item + 1] - P.slot_base[item])
             have = fresh = false;  // staged: the copy kernel wrote it
         }
+        u = ip.u;
+        seg = ip.seg;
       }
-      next += taken < avail ? taken : avail;
+      const long long adv = taken < avail ? taken : avail;
+      next += adv;
+      if (!(MODE == MODE_EMIT && list_mode) && next < tend) {
+        if (SINGLE)
+          cpos = item_advance(G1, cpos, adv);
+        else
+          cursor_advance(P.graphs, cg, cpos, adv);
+      }
       need = __ballot_sync(FULL_MASK, !have);
     }
     if (!__any_sync(FULL_MASK, have)) {
@@ -216,16 +245,13 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
     if (have && fresh) {
       unsigned j0;
       if (SINGLE) {
-        item_bounds(G1, item, u, seg, j0, end);
+        pos_bounds(G1, ItemPos{0, u, seg}, j0, end);
       } else {
-        int gi = graph_of_item(P.graphs, P.G, item);
-        gi_l = gi;
-        const DevGraph& g = P.graphs[gi];
-        item_bounds(g, item - g.item_begin, u, seg, j0, end);
+        const DevGraph& g = P.graphs[gi_l];
+        pos_bounds(g, ItemPos{0, u, seg}, j0, end);
         w_l = (const w_t*)g.w;
         S_l = T::S(g);
-        Sh_l = g.S_ff_hi;
-        Sl_l = g.S_ff_lo;
+        lc_l = LpConst{g.lp_zS, g.lp_sh, g.lp_cS};
         k0_l = g.key0;
         k1_l = g.key1;
       }
@@ -315,7 +341,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         if (Qt == 0)
           done = true;  // p = 0: no further edge
         else if (Qt < S)
-          Lp = T::Lp(Qt, S, SINGLE ? ff{G1.S_ff_hi, G1.S_ff_lo} : ff{Sh_l, Sl_l});
+          Lp = T::Lp(Qt, S, SINGLE ? LpConst{G1.lp_zS, G1.lp_sh, G1.lp_cS} : lc_l);
       }
       j = fresh ? target : target + 1;
       if (j >= end) done = true;
@@ -381,6 +407,9 @@ __global__ void __launch_bounds__(COPY_THREADS) copy_kernel(DevPlan P, long long
     long long i0 = ib + (long long)c * 32;
     if (i0 >= ie) break;
     long long i = i0 + lane;
+    // position of the warp's first item (warp-uniform); lanes step from it
+    const int g0 = P.G == 1 ? 0 : graph_of_item(P.graphs, P.G, i0);
+    const ItemPos p0 = item_pos(P.graphs[g0], i0 - P.graphs[g0].item_begin);
     long long o = 0, pos = 0;
     int cnt = 0;
     unsigned uu = 0;
@@ -390,10 +419,10 @@ __global__ void __launch_bounds__(COPY_THREADS) copy_kernel(DevPlan P, long long
       pos = P.slot_base[i];
       if (cc <= P.slot_base[i + 1] - pos) cnt = (int)cc;  // else: not staged, regenerated
       if (cnt > 0) {
-        int gi = P.G == 1 ? 0 : graph_of_item(P.graphs, P.G, i);
-        const DevGraph& g = P.graphs[gi];
-        unsigned sg, j0, en;
-        item_bounds(g, i - g.item_begin, uu, sg, j0, en);
+        int gi = g0;
+        ItemPos ip = p0;
+        cursor_advance(P.graphs, gi, ip, lane);
+        uu = ip.u;
       }
     }
     int incl = cnt;
