@@ -289,10 +289,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     } else {
       d.S_i = (long long)res[g].S_i;
       d.S_d = (double)d.S_i;
-      const LpConst lc = lp_const((unsigned long long)d.S_i);  // for the per-candidate -ln(1 - p)
-      d.lp_zS = lc.zS;
-      d.lp_sh = lc.sh;
-      d.lp_cS = lc.cS;
+      d.lp = lp_const((unsigned long long)d.S_i);  // for the per-candidate -ln(1 - p)
       if (gs == CL_OK && res[g].S_i >= (1ull << 53)) gs = CL_ERR_RANGE;
     }
     d.invS_f = d.S_d > 0 ? (float)(1.0 / d.S_d) : 0.0f;

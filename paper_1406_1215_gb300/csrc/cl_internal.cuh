@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "../../include/cl.h"
@@ -13,10 +14,15 @@ constexpr unsigned LIGHT_SEG = 0xFFFFFFFFu;
 constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
 
 // Per-graph constants of -ln(1 - Q/S): zS = clz(S), sh = max(0, 41 - zS)
-// (so S >> sh has at most 23 bits) and cS = 64 / (S >> sh) in float.
+// (so S >> sh has at most 23 bits), cS = 64 / (S >> sh) in float, the
+// series bound Ssmall = S >> 12 (p < 2^-12 below it) and 1/S as a
+// float-float pair (hi = 1/S rounded to float, lo = the rounded remainder,
+// formed from the exact integer 2^k - m S).
 struct LpConst {
   int zS, sh;
   float cS;
+  float iS_hi, iS_lo;
+  unsigned long long Ssmall;
 };
 __host__ __device__ inline LpConst lp_const(unsigned long long S) {
 #ifdef __CUDA_ARCH__
@@ -25,7 +31,19 @@ __host__ __device__ inline LpConst lp_const(unsigned long long S) {
   const int z = S ? __builtin_clzll(S) : 64;
 #endif
   const int sh = z < 41 ? 41 - z : 0;
-  return LpConst{z, sh, (float)(64.0 / (double)(S >> sh))};
+  LpConst c{z, sh, (float)(64.0 / (double)(S >> sh)), 0.0f, 0.0f, S >> 12};
+  if (S > 0) {
+    const float hi = (float)(1.0 / (double)S);
+    int ex;
+    const double m = frexp((double)hi, &ex);  // hi = m 2^ex, m in [1/2, 1)
+    const long long M = (long long)ldexp(m, 24);
+    const int k = 24 - ex;  // hi = M 2^-k, 2^k > M S since hi ~ 1/S
+    // remainder 1 - hi S = (2^k - M S) 2^-k, exact in 128-bit integers (k < 90)
+    const __int128 num = ((__int128)1 << k) - (__int128)M * (__int128)S;
+    c.iS_hi = hi;
+    c.iS_lo = (float)(ldexp((double)num, -k) / (double)S);
+  }
+  return c;
 }
 
 // One graph of a plan, as the kernels see it (lives in the plan workspace).
@@ -42,8 +60,7 @@ struct DevGraph {
   long long n_items;      // items of this graph
   long long pbase;        // offset of this graph's weight prefix (n + 1 entries)
   int wtype;              // cl_wtype
-  int lp_zS, lp_sh;       // constants of -ln(1 - Q/S) (integer weights, see lp_const)
-  float lp_cS;
+  LpConst lp;             // constants of -ln(1 - Q/S) (integer weights)
   float invS_f;           // 1 / S in single precision (costs only)
   long long bbase;        // offset of this graph's entries in the uniform-block table (integer weights)
 };

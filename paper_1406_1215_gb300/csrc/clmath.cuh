@@ -29,6 +29,7 @@
 #pragma once
 #include <cstdint>
 
+#include "cl_internal.cuh"
 #include "ln_tables.h"
 
 namespace cl {
@@ -191,7 +192,7 @@ __device__ __forceinline__ ff ff_neglog_r53(unsigned long long A) {
 //   -ln(A/S) = e ln2 + ln(64/J) - 2 atanh(N/D).
 // For p < 1/2048 this is e = 0, J = 64, N = -64 Q: the pure atanh series,
 // with full relative precision however small p is.
-__device__ __forceinline__ ff ff_neglog1m(unsigned long long Q, unsigned long long S, LpConst c) {
+__device__ __forceinline__ ff ff_neglog1m_table(unsigned long long Q, unsigned long long S, const LpConst& c) {
   const unsigned long long A = S - Q;
   const int e = __clzll(A) - c.zS;
   const unsigned long long Ap = A << e;
@@ -440,6 +441,29 @@ static __device__ __noinline__ long long skip_fallback_dd(unsigned long long Ar,
   dd Lr = dd_neglog_ratio(Ar, 1ull << 53);
   dd Lp = dd_neglog_ratio(Ap, S);
   return floor_decide_dd(dd_div(Lr, Lp), R, tie);
+}
+
+// -ln(1 - p) for p = Q/S < 2^-12 by its series p (1 + c),
+// c = p/2 + p^2/3 + p^3/4 (the next term, p^4/5, is below 2^-50 p):
+// p = Q (1/S) as float-float (Q exact below 2^46, 1/S to ~2^-48), c as a
+// float pair (p/2 exactly, the rest rounded at ~2^-50), p c with an exact
+// product of the leading parts.
+__device__ __forceinline__ ff ff_neglog1m_small(unsigned long long Q, const LpConst& c) {
+  const ff p = ff_mul(ff_from_u64(Q), ff{c.iS_hi, c.iS_lo});
+  const float ch = 0.5f * p.hi;
+  const float cl = fmaf(p.hi * p.hi, fmaf(p.hi, 0.25f, 1.0f / 3.0f), 0.5f * p.lo);
+  ff pc = ff_two_prod(p.hi, ch);
+  pc.lo = fmaf(p.hi, cl, fmaf(p.lo, ch, pc.lo));
+  ff L = ff_fast_two_sum(p.hi, pc.hi);
+  L.lo = __fadd_rn(L.lo, __fadd_rn(p.lo, pc.lo));
+  return L;
+}
+
+// -ln(1 - Q/S), 0 < Q < S < 2^53: the series for p < 2^-12 (most candidates
+// of a power-law graph; lanes of a warp mostly agree), the table otherwise.
+__device__ __forceinline__ ff ff_neglog1m(unsigned long long Q, unsigned long long S, const LpConst& c) {
+  if (Q < c.Ssmall) return ff_neglog1m_small(Q, c);
+  return ff_neglog1m_table(Q, S, c);
 }
 
 }  // namespace cl

@@ -72,7 +72,7 @@ struct Wt<false> {
     q_t q = (q_t)((long long)a * (long long)b);
     return q < S ? q : S;
   }
-  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, LpConst c) { return ff_neglog1m(Q, S, c); }
+  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, const LpConst& c) { return ff_neglog1m(Q, S, c); }
   static __device__ __forceinline__ long long skip1(ff Lr, lp_t Lp, long long R) {
     return floor_decide_ff(ff_div(Lr, Lp), R);
   }
@@ -93,7 +93,7 @@ struct Wt<true> {
     q_t q = a * b;
     return q >= S ? S : q;  // capped iff the rounded product reaches S
   }
-  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, LpConst) { return d_neglog1m(Q, S); }
+  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, const LpConst&) { return d_neglog1m(Q, S); }
   static __device__ __forceinline__ long long skip1(ff Lr, lp_t Lp, long long R) {
     return floor_decide_d(((double)Lr.hi + (double)Lr.lo) / Lp, R);
   }
@@ -154,7 +154,6 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   int gi_l = 0;
   const w_t* w_l = nullptr;
   q_t S_l = 0;
-  LpConst lc_l{0, 0, 0.f};
   unsigned k0_l = 0, k1_l = 0;
   unsigned long long sbase = 0;  // staging: the item's slot and its size
   unsigned ssize = 0;
@@ -251,7 +250,6 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         pos_bounds(g, ItemPos{0, u, seg}, j0, end);
         w_l = (const w_t*)g.w;
         S_l = T::S(g);
-        lc_l = LpConst{g.lp_zS, g.lp_sh, g.lp_cS};
         k0_l = g.key0;
         k1_l = g.key1;
       }
@@ -341,7 +339,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         if (Qt == 0)
           done = true;  // p = 0: no further edge
         else if (Qt < S)
-          Lp = T::Lp(Qt, S, SINGLE ? LpConst{G1.lp_zS, G1.lp_sh, G1.lp_cS} : lc_l);
+          Lp = T::Lp(Qt, S, SINGLE ? G1.lp : P.graphs[gi_l].lp);
       }
       j = fresh ? target : target + 1;
       if (j >= end) done = true;
