@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   long long next = 0, tend = 0;
   bool tasks_left = true;
   int cg = 0;
-  ItemPos cpos{0, 0u, 0u};
+  unsigned cu = 0, cseg = 0;  // row and segment of item `next` (its local index is next - item_begin)
   // lane state
   bool have = false, fresh = false;
   long long item = 0, obase = 0;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   q_t Qprev = 0;
   typename T::lp_t Lp{};
   w_t wu = 0;
-  u32x4 pb{0u, 0u, 0u, 0u};  // the lane's next draw (index t) ...
+  unsigned pz = 0, pw = 0;   // the lane's next draw (index t): acceptance words ...
   ff pLr{0.f, 0.f};          // ... and its -ln r_s
   // the lane's current weight run (integer weights): candidates before run_end weigh run_w
   unsigned run_end = 0;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   unsigned long long sbase = 0;  // staging: the item's slot and its size
   unsigned ssize = 0;
   __shared__ unsigned sgrp[MODE == MODE_STAGE ? GROUP : 1][SAMPLER_THREADS];  // staging group, [entry][thread]
-  unsigned long long n_iter = 0, n_fb = 0, n_tie = 0;
+  unsigned n_iter = 0;  // loop iterations of the lane (fallbacks and ties go straight to the stats)
 
   while (true) {
     // ---- (1) lanes without an item take the next items of the warp's task
@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         if (next < tend) {  // position of the task's first item (once per task, warp-uniform)
           cg = SINGLE ? 0 : graph_of_item(P.graphs, P.G, next);
           const DevGraph& g = SINGLE ? G1 : P.graphs[cg];
-          cpos = item_pos(g, next - g.item_begin);
+          const ItemPos cp = item_pos(g, next - g.item_begin);
+          cu = cp.u;
+          cseg = cp.seg;
         }
         continue;
       }
@@ -210,8 +212,8 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
           }
         } else {  // consecutive items: a few steps from the warp's cursor
           item = next + rank;
-          ip = cpos;
           gi_l = cg;
+          ip = ItemPos{next - (SINGLE ? 0ll : P.graphs[cg].item_begin), cu, cseg};
           if (SINGLE)
             ip = item_advance(G1, ip, rank);
           else
@@ -226,10 +228,13 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       const long long adv = taken < avail ? taken : avail;
       next += adv;
       if (!(MODE == MODE_EMIT && list_mode) && next < tend) {
+        ItemPos cp{next - adv - (SINGLE ? 0ll : P.graphs[cg].item_begin), cu, cseg};
         if (SINGLE)
-          cpos = item_advance(G1, cpos, adv);
+          cp = item_advance(G1, cp, adv);
         else
-          cursor_advance(P.graphs, cg, cpos, adv);
+          cursor_advance(P.graphs, cg, cp, adv);
+        cu = cp.u;
+        cseg = cp.seg;
       }
       need = __ballot_sync(FULL_MASK, !have);
     }
@@ -268,7 +273,6 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
     const w_t* W = SINGLE ? (const w_t*)G1.w : w_l;
     const q_t S = SINGLE ? T::S(G1) : S_l;
     // ---- (3) one skip for running items, with the precomputed draw t
-    const u32x4 cur = pb;
     if (have && !fresh) {
       ++t;
       ++n_iter;
@@ -278,9 +282,11 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         delta = T::skip1(pLr, Lp, R);
         if (delta == SKIP_UNDECIDED) {
           bool tie;
-          delta = T::skip2(2ull * grid52(cur.x, cur.y) + 1ull, Qprev, S, R, &tie);
-          ++n_fb;
-          n_tie += tie;
+          // rare: regenerate the draw's skip words rather than keep them in registers
+          const u32x4 d = philox4x32_10(u32x4{t - 1u, seg, u, 0u}, SINGLE ? G1.key0 : k0_l, SINGLE ? G1.key1 : k1_l);
+          delta = T::skip2(2ull * grid52(d.x, d.y) + 1ull, Qprev, S, R, &tie);
+          atomicAdd(&P.stats[1], 1ull);
+          if (tie) atomicAdd(&P.stats[2], 1ull);
         }
       }
       if (delta >= R) {
@@ -299,12 +305,17 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         const long long bbase = SINGLE ? G1.bbase : P.graphs[gi_l].bbase;
         wt = (w_t)block_weight(P, (const int*)W, bbase, target, run_end, run_w);
       }
-      pb = philox4x32_10(u32x4{t, seg, u, 0u}, SINGLE ? G1.key0 : k0_l, SINGLE ? G1.key1 : k1_l);
-      pLr = ff_neglog_r53(2ull * grid52(pb.x, pb.y) + 1ull);
+      const unsigned az = pz, aw = pw;  // acceptance words of the draw that made the candidate
+      {
+        const u32x4 nb = philox4x32_10(u32x4{t, seg, u, 0u}, SINGLE ? G1.key0 : k0_l, SINGLE ? G1.key1 : k1_l);
+        pz = nb.z;
+        pw = nb.w;
+        pLr = ff_neglog_r53(2ull * grid52(nb.x, nb.y) + 1ull);
+      }
       const q_t Qt = T::Q(wu, wt, S);
       // ---- (5) acceptance r_a < q / p, with the draw that made the candidate
       if (!fresh) {
-        bool acc = (Qt == Qprev) || T::accept(grid52(cur.z, cur.w), Qprev, Qt);
+        bool acc = (Qt == Qprev) || T::accept(grid52(az, aw), Qprev, Qt);
         if (acc) {
           if (MODE == MODE_EMIT) {
             long long pos = obase + k;
@@ -366,17 +377,14 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       have = false;
     }
   }
+  unsigned long long n_iter64 = n_iter;
   if (MODE != MODE_EMIT) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      n_iter += __shfl_xor_sync(FULL_MASK, n_iter, o);
-      n_fb += __shfl_xor_sync(FULL_MASK, n_fb, o);
-      n_tie += __shfl_xor_sync(FULL_MASK, n_tie, o);
+      n_iter64 += __shfl_xor_sync(FULL_MASK, n_iter64, o);
     }
     if (lane == 0) {
-      atomicAdd(&P.stats[0], n_iter);
-      if (n_fb) atomicAdd(&P.stats[1], n_fb);
-      if (n_tie) atomicAdd(&P.stats[2], n_tie);
+      atomicAdd(&P.stats[0], n_iter64);
     }
   }
 }
