@@ -257,10 +257,9 @@ def run_ours(args, rank: int, world: int):
             w_dev.copy_(w_host, non_blocking=True)
             pl = P.cl_plan_create([graph2], tun, scratch, sb, sh)
             P.cl_plan_build(pl, ws, wb, sh)
-            P.cl_count(pl, counts, sh)
-            mm = P.cl_scan(pl, counts, offsets, True, sh)
-            P.cl_emit(pl, offsets, P.CL_E_I32, edges, cap, 0, n_items, sh)
-            out_host[:mm].copy_(edges[:mm], non_blocking=True)
+            # count + scan + emit with the edges stored straight into pinned host memory,
+            # the host writes of one item range overlapping the count of the next
+            mm = P.cl_generate_host(pl, P.CL_E_I32, out_host, cap, counts, offsets, 0, 0, sh)
             P.cl_plan_destroy(pl)
             return mm
 

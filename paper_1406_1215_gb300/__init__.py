@@ -21,6 +21,8 @@ STATUS_NAMES = {
     5: "CL_ERR_CAPACITY", 6: "CL_ERR_WORKSPACE", 7: "CL_ERR_TIMEOUT", 8: "CL_ERR_CUDA", 9: "CL_ERR_STATE",
     10: "CL_ERR_DEVICE",
 }
+(CL_ERR_INVALID_ARG, CL_ERR_UNSORTED, CL_ERR_NONFINITE, CL_ERR_RANGE, CL_ERR_CAPACITY, CL_ERR_WORKSPACE,
+ CL_ERR_TIMEOUT, CL_ERR_CUDA, CL_ERR_STATE, CL_ERR_DEVICE) = range(1, 11)
 CL_W_I32, CL_W_F64 = 0, 1
 CL_E_I32, CL_E_I64 = 0, 1
 HEAVY_W_DEFAULT = 8192.0
@@ -87,6 +89,7 @@ def load_library(path: str | None = None):
         "cl_scan": ([vp, vp, vp, P(i64), vp], i32),
         "cl_emit": ([vp, vp, i32, vp, i64, i64, i64, vp], i32),
         "cl_generate_batch": ([vp, i32, vp, i64, vp, vp, vp, vp, vp], i32),
+        "cl_generate_host": ([vp, i32, vp, i64, vp, vp, i32, i32, P(i64), vp], i32),
         "cl_stats": ([vp, P(cl_run_stats), vp], i32),
         "cl_check": ([vp, vp], i32),
         "cl_plan_destroy": ([vp], None),
@@ -201,6 +204,16 @@ def cl_generate_batch(plan, etype: int, d_edges, capacity: int, d_graph_offsets,
     st = load_library().cl_generate_batch(plan, etype, _ptr(d_edges), capacity, _ptr(d_graph_offsets),
                                           _ptr(d_counts), _ptr(d_offsets), _ptr(d_status), _stream(stream))
     _check(st, "cl_generate_batch")
+
+
+def cl_generate_host(plan, etype: int, h_edges, capacity: int, d_counts, d_offsets, chunks: int = 0,
+                     copy_sms: int = 0, stream=None) -> int:
+    """Whole plan to page-locked host memory (h_edges: pinned tensor or address); returns m."""
+    m = ctypes.c_int64(0)
+    st = load_library().cl_generate_host(plan, etype, _ptr(h_edges), capacity, _ptr(d_counts), _ptr(d_offsets),
+                                         chunks, copy_sms, ctypes.byref(m), _stream(stream))
+    _check(st, "cl_generate_host")
+    return m.value
 
 
 def cl_stats(plan, stream=None) -> dict:

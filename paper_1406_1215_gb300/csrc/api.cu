@@ -54,6 +54,10 @@ struct cl_plan {
   long long* d_ovf_list = nullptr;
   unsigned* d_ovf_count = nullptr;
   unsigned long long* d_blk = nullptr;
+  unsigned* d_snap = nullptr;  // per-chunk snapshots of the regeneration list length
+  // host-output pipeline (cl_generate_host): a second stream and its events, made on first use
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> events;
 };
 
 namespace {
@@ -125,6 +129,7 @@ struct WsLayout {
   long long* ovf_list;
   unsigned* ovf_count;
   unsigned long long* blk;
+  unsigned* snap;
   unsigned* pool;
   size_t bytes;
 };
@@ -151,6 +156,7 @@ WsLayout ws_layout(void* base, const cl_plan* p) {
   L.ovf_count = c.take<unsigned>(4);
   const bool runs = p->wtype == CL_W_I32;
   L.blk = runs ? c.take<unsigned long long>(p->csize > 0 ? p->csize : 1) : nullptr;
+  L.snap = c.take<unsigned>(CL_HOST_MAX_CHUNKS);
   L.pool = p->stage ? c.take<unsigned>(p->pool_cap > 0 ? p->pool_cap : 1) : nullptr;
   L.bytes = c.off;
   return L;
@@ -398,6 +404,7 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   p->d_ovf_list = L.ovf_list;
   p->d_ovf_count = L.ovf_count;
   p->d_blk = L.blk;
+  p->d_snap = L.snap;
   cl_status st;
   if ((st = cuda_ok(cudaMemcpyAsync(L.graphs, p->dg.data(), sizeof(DevGraph) * p->G, cudaMemcpyHostToDevice, s))))
     return st;
@@ -467,8 +474,9 @@ cl_status cl_emit(cl_plan* p, const int64_t* d_offsets, int32_t etype, void* d_e
   if (!p->built) return CL_ERR_STATE;
   if (item_end == item_begin) return CL_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  launch_emit(dev_plan(p), p->G == 1 ? &p->dg[0] : nullptr, (const long long*)d_offsets, item_begin, item_end, etype,
-              d_edges, capacity, p->staged, p->block, etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, s);
+  launch_emit(dev_plan(p), p->G == 1 ? &p->dg[0] : nullptr, (const long long*)d_offsets,
+              SampleRange{item_begin, item_end, 0, item_begin}, etype, d_edges, capacity, p->staged, p->block,
+              etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, 0, s);
   return last_ok();
 }
 
@@ -487,8 +495,9 @@ cl_status cl_generate_batch(cl_plan* p, int32_t etype, void* d_edges, int64_t ca
                        capacity, d_status, s);
   if ((st = last_ok())) return st;
   if (p->n_items == 0) return CL_OK;
-  launch_emit(dev_plan(p), p->G == 1 ? &p->dg[0] : nullptr, (const long long*)d_offsets, 0, p->n_items, etype,
-              d_edges, capacity, p->staged, p->block, etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, s);
+  launch_emit(dev_plan(p), p->G == 1 ? &p->dg[0] : nullptr, (const long long*)d_offsets,
+              SampleRange{0, p->n_items, 0, 0}, etype, d_edges, capacity, p->staged, p->block,
+              etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64, 0, s);
   return last_ok();
 }
 
@@ -523,6 +532,96 @@ cl_status cl_check(cl_plan* p, cl_stream_t stream) {
   return (cl_status)err;
 }
 
-void cl_plan_destroy(cl_plan* p) { delete p; }
+cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t capacity, int32_t* d_counts,
+                           int64_t* d_offsets, int32_t chunks, int32_t copy_sms, int64_t* h_total,
+                           cl_stream_t stream) {
+  if (!p || !d_offsets || !h_total || capacity < 0) return CL_ERR_INVALID_ARG;
+  if (etype != CL_E_I32 && etype != CL_E_I64) return CL_ERR_INVALID_ARG;
+  if (p->n_items > 0 && !d_counts) return CL_ERR_INVALID_ARG;
+  if (capacity > 0 && !h_edges) return CL_ERR_INVALID_ARG;
+  if (chunks < 0 || chunks > CL_HOST_MAX_CHUNKS || copy_sms < 0) return CL_ERR_INVALID_ARG;
+  if (!p->built) return CL_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cl_status st;
+  *h_total = 0;
+  // the kernels store edges through the mapped device address of the host buffer
+  void* d_edges = nullptr;
+  if (capacity > 0 && cudaHostGetDevicePointer(&d_edges, h_edges, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return CL_ERR_INVALID_ARG;  // not page-locked, device-mapped host memory
+  }
+  if ((st = cuda_ok(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s)))) return st;
+  if (p->n_items == 0) return cuda_ok(cudaStreamSynchronize(s));
+  const int C = chunks == 0 ? 8 : (chunks > p->T ? p->T : chunks);
+  int reserve = copy_sms == 0 ? (p->sms >= 32 ? 16 : p->sms / 2) : copy_sms;
+  if (reserve >= p->sms) reserve = p->sms - 1;
+  if (reserve < 1) reserve = 1;
+  if (!p->side && (st = cuda_ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)))) return st;
+  while ((int)p->events.size() < C + 1) {
+    cudaEvent_t e;
+    if ((st = cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)))) return st;
+    p->events.push_back(e);
+  }
+  // chunk c: tasks [tc_c, tc_{c+1}) of Eq. 3 (equal cost), items [task_start[tc_c], task_start[tc_{c+1}])
+  std::vector<int> tc(C + 1);
+  std::vector<long long> ic(C + 1);
+  for (int c = 0; c <= C; ++c) tc[c] = (int)((long long)p->T * c / C);
+  for (int c = 0; c < C; ++c)
+    if ((st = cuda_ok(cudaMemcpyAsync(&ic[c], p->d_task + tc[c], sizeof(long long), cudaMemcpyDeviceToHost, s))))
+      return st;
+  if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
+  ic[C] = p->n_items;
+  const DevGraph* single = p->G == 1 ? &p->dg[0] : nullptr;
+  const DevPlan P = dev_plan(p);
+  const int bps = p->grid_count / (p->sms > 0 ? p->sms : 1);
+  const int grid_count = (bps > 0 ? bps : 1) * (p->sms - reserve);
+  const int grid_side = (bps > 0 ? bps : 1) * reserve;
+  cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s);
+  if (p->stage) {
+    cudaMemsetAsync(P.overflow, 0, sizeof(int), s);
+    cudaMemsetAsync(P.ovf_count, 0, sizeof(unsigned), s);
+  }
+  for (int c = 0; c < C; ++c) {
+    const long long ib = ic[c], ie = ic[c + 1];
+    if (ie > ib) {
+      launch_count_range(P, single, d_counts, p->stage, SampleRange{ib, ie, tc[c], ib}, p->block, grid_count, s);
+      if (p->stage)  // the regeneration list as it stands after this chunk's count
+        cudaMemcpyAsync(p->d_snap + c, P.ovf_count, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
+      launch_count_scan(d_counts + ib, ie - ib, (long long*)d_offsets + ib, p->d_scan_part, s,
+                        (const long long*)d_offsets + ib);
+    }
+    if ((st = last_ok())) return st;
+    cudaEventRecord(p->events[c], s);
+    if (ie == ib) continue;
+    // this chunk's edges go out over the host link while the next chunk is counted
+    cudaStreamWaitEvent(p->side, p->events[c], 0);
+    DevPlan Ps = P;
+    Ps.task_ctr = P.task_ctr + 1;  // its own work counter
+    Ps.ovf_count = p->d_snap + c;
+    launch_emit(Ps, single, (const long long*)d_offsets, SampleRange{ib, ie, tc[c], 0}, etype, d_edges, capacity,
+                p->stage, p->block, grid_side, grid_side, p->side);
+    if ((st = last_ok())) return st;
+  }
+  p->staged = p->stage;
+  cudaEventRecord(p->events[C], p->side);
+  cudaStreamWaitEvent(s, p->events[C], 0);
+  int err = 0;
+  if ((st = cuda_ok(cudaMemcpyAsync(h_total, d_offsets + p->n_items, sizeof(int64_t), cudaMemcpyDeviceToHost, s))))
+    return st;
+  if ((st = cuda_ok(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)))) return st;
+  if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
+  if (*h_total > capacity) return CL_ERR_CAPACITY;
+  return err ? (cl_status)err : CL_OK;
+}
+
+void cl_plan_destroy(cl_plan* p) {
+  if (!p) return;
+  if (p->side) {
+    cudaStreamSynchronize(p->side);
+    cudaStreamDestroy(p->side);
+  }
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  delete p;
+}
 
 }  // extern "C"

@@ -226,16 +226,31 @@ void launch_blocks(const DevGraph* d_graphs, int G, long long nblk, unsigned lon
 void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, bool f64, const void* d_P,
                             long long* d_C, long long* d_partials, long long* d_task_start, int T, int* d_slot32,
                             int tiny_slots, cudaStream_t s);
-// Exclusive int32 -> int64 scan with the total at out[n].
+// Exclusive int32 -> int64 scan with the total at out[n]; with d_base, every
+// output is offset by *d_base (read on the device: a scan of a later range of
+// items continues from the total of the earlier ones, with no host round trip).
 void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, long long* d_partials,
-                       cudaStream_t s);
+                       cudaStream_t s, const long long* d_base = nullptr);
 long long scan_partials_needed(long long n);
+
+// Items [ib, ie) of a sampling launch; tasks are taken from t0 on (the first
+// task that reaches ib), and edges[0] of an emitting launch holds the first
+// edge of item ob (ob = ib: the range's own array; ob = 0: absolute offsets).
+struct SampleRange {
+  long long ib, ie;
+  int t0;
+  long long ob;
+};
 
 // `single`: host copy of the plan's only graph (G == 1), passed to the kernels by value; else nullptr
 void launch_count(const DevPlan& P, const DevGraph* single, int* d_counts, bool stage, int block, int grid,
                   cudaStream_t s);
-void launch_emit(const DevPlan& P, const DevGraph* single, const long long* d_offsets, long long ib, long long ie,
-                 int etype, void* d_edges, long long capacity, bool staged, int block, int grid, cudaStream_t s);
+void launch_count_range(const DevPlan& P, const DevGraph* single, int* d_counts, bool stage, const SampleRange& r,
+                        int block, int grid, cudaStream_t s);
+// copy_grid > 0 caps the copy kernel's grid (to leave SMs to a concurrent launch)
+void launch_emit(const DevPlan& P, const DevGraph* single, const long long* d_offsets, const SampleRange& r,
+                 int etype, void* d_edges, long long capacity, bool staged, int block, int grid, int copy_grid,
+                 cudaStream_t s);
 void launch_graph_offsets(const DevGraph* d_graphs, int G, const long long* d_offsets, long long n_items,
                           long long* d_graph_offsets, long long capacity, int* d_status, cudaStream_t s);
 int sampler_max_blocks_per_sm(int block, bool emit, int etype);

@@ -531,7 +531,9 @@ __global__ void __launch_bounds__(PLAN_THREADS) count_reduce_kernel(const int* _
 
 __global__ void __launch_bounds__(PLAN_THREADS) count_scan_kernel(const int* __restrict__ x, long long n,
                                                                   const long long* __restrict__ part,
-                                                                  long long* __restrict__ out, long long nt) {
+                                                                  long long* __restrict__ out, long long nt,
+                                                                  const long long* base) {
+  const long long b0 = base ? *base : 0;  // out[0] == *base when base == out: rewritten unchanged
   long long i0 = blockIdx.x * (long long)SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
   int v[SCAN_ITEMS];
   long long loc = 0;
@@ -541,25 +543,25 @@ __global__ void __launch_bounds__(PLAN_THREADS) count_scan_kernel(const int* __r
     loc += v[k];
   }
   long long tot;
-  long long run = block_excl_scan(loc, &tot) + part[blockIdx.x];
+  long long run = block_excl_scan(loc, &tot) + part[blockIdx.x] + b0;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
     if (i0 + k < n) out[i0 + k] = run;
     run += v[k];
   }
-  if (blockIdx.x == nt - 1 && threadIdx.x == 0) out[n] = part[blockIdx.x] + tot;
+  if (blockIdx.x == nt - 1 && threadIdx.x == 0) out[n] = part[blockIdx.x] + tot + b0;
 }
 
 void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, long long* d_partials,
-                       cudaStream_t s) {
+                       cudaStream_t s, const long long* d_base) {
   if (n <= 0) {
-    cudaMemsetAsync(d_offsets, 0, sizeof(long long), s);
+    if (!d_base) cudaMemsetAsync(d_offsets, 0, sizeof(long long), s);
     return;
   }
   long long nt = (n + SCAN_TILE - 1) / SCAN_TILE;
   count_reduce_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_counts, n, d_partials);
   partials_scan_kernel<long long><<<1, 1024, 0, s>>>(d_partials, nt, nullptr);
-  count_scan_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_counts, n, d_partials, d_offsets, nt);
+  count_scan_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_counts, n, d_partials, d_offsets, nt, d_base);
 }
 
 }  // namespace cl

@@ -109,7 +109,8 @@ struct Wt<true> {
 template <int MODE, bool SINGLE, bool WF, typename E>
 __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
     sample_kernel(DevPlan P, DevGraph G1, long long ib, long long ie, const long long* __restrict__ offsets,
-                  E* __restrict__ edges, long long capacity, int* __restrict__ counts, int regen_only) {
+                  E* __restrict__ edges, long long capacity, int* __restrict__ counts, int regen_only, int t0,
+                  long long ob) {
   using T = Wt<WF>;
   using w_t = typename T::w_t;
   using q_t = typename T::q_t;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         n_list = nov;
       }
     }
-    off_base = offsets[ib];
+    off_base = offsets[ob];  // edges[0] holds the first edge of item ob
     if (offsets[ie] - off_base > capacity) {
       if (blockIdx.x == 0 && threadIdx.x == 0) set_error(P.err, CL_ERR_CAPACITY);
       return;  // nothing is written when the range does not fit
@@ -178,7 +179,8 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
           tend = next + 32 < n_list ? next + 32 : n_list;
           continue;
         }
-        if (tix >= (unsigned)P.T) {
+        tix += (unsigned)t0;  // the range's first task
+        if (tix >= (unsigned)P.T || P.task_start[tix] >= ie) {
           tasks_left = false;
           break;
         }
@@ -397,11 +399,11 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
 constexpr int COPY_THREADS = 256;
 
 template <typename E>
-__global__ void __launch_bounds__(COPY_THREADS) copy_kernel(DevPlan P, long long ib, long long ie,
+__global__ void __launch_bounds__(COPY_THREADS) copy_kernel(DevPlan P, long long ib, long long ie, long long ob,
                                                             const long long* __restrict__ offsets,
                                                             E* __restrict__ edges, long long capacity) {
   const int lane = threadIdx.x & 31;
-  const long long off_base = offsets[ib];
+  const long long off_base = offsets[ob];  // edges[0] holds the first edge of item ob
   if (offsets[ie] - off_base > capacity) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_error(P.err, CL_ERR_CAPACITY);
     return;
@@ -493,61 +495,69 @@ int sampler_max_blocks_per_sm(int block, bool emit, int etype) {
 }
 
 template <int MODE, bool WF, typename E>
-static void launch_sampler_w(const DevPlan& P, const DevGraph* single, long long ib, long long ie,
-                             const long long* offsets, E* edges, long long capacity, int* counts, int regen,
-                             int block, int grid, cudaStream_t s) {
+static void launch_sampler_w(const DevPlan& P, const DevGraph* single, const SampleRange& r, const long long* offsets,
+                             E* edges, long long capacity, int* counts, int regen, int block, int grid,
+                             cudaStream_t s) {
   if (single)
-    sample_kernel<MODE, true, WF, E>
-        <<<grid, block, 0, s>>>(P, *single, ib, ie, offsets, edges, capacity, counts, regen);
+    sample_kernel<MODE, true, WF, E><<<grid, block, 0, s>>>(P, *single, r.ib, r.ie, offsets, edges, capacity, counts,
+                                                            regen, r.t0, r.ob);
   else
-    sample_kernel<MODE, false, WF, E>
-        <<<grid, block, 0, s>>>(P, DevGraph{}, ib, ie, offsets, edges, capacity, counts, regen);
+    sample_kernel<MODE, false, WF, E><<<grid, block, 0, s>>>(P, DevGraph{}, r.ib, r.ie, offsets, edges, capacity,
+                                                             counts, regen, r.t0, r.ob);
 }
 
 template <int MODE, typename E>
-static void launch_sampler(const DevPlan& P, const DevGraph* single, long long ib, long long ie,
-                           const long long* offsets, E* edges, long long capacity, int* counts, int regen, int block,
-                           int grid, cudaStream_t s) {
+static void launch_sampler(const DevPlan& P, const DevGraph* single, const SampleRange& r, const long long* offsets,
+                           E* edges, long long capacity, int* counts, int regen, int block, int grid,
+                           cudaStream_t s) {
   if (P.wf64)
-    launch_sampler_w<MODE, true, E>(P, single, ib, ie, offsets, edges, capacity, counts, regen, block, grid, s);
+    launch_sampler_w<MODE, true, E>(P, single, r, offsets, edges, capacity, counts, regen, block, grid, s);
   else
-    launch_sampler_w<MODE, false, E>(P, single, ib, ie, offsets, edges, capacity, counts, regen, block, grid, s);
+    launch_sampler_w<MODE, false, E>(P, single, r, offsets, edges, capacity, counts, regen, block, grid, s);
 }
 
 void launch_count(const DevPlan& P, const DevGraph* single, int* d_counts, bool stage, int block, int grid,
                   cudaStream_t s) {
-  cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
   if (stage) {
     cudaMemsetAsync(P.overflow, 0, sizeof(int), s);
     cudaMemsetAsync(P.ovf_count, 0, sizeof(unsigned), s);
-    launch_sampler<MODE_STAGE, int2>(P, single, 0, P.n_items, nullptr, nullptr, 0, d_counts, 0, block, grid, s);
-  } else {
-    launch_sampler<MODE_COUNT, int2>(P, single, 0, P.n_items, nullptr, nullptr, 0, d_counts, 0, block, grid, s);
   }
+  launch_count_range(P, single, d_counts, stage, SampleRange{0, P.n_items, 0, 0}, block, grid, s);
 }
 
-void launch_emit(const DevPlan& P, const DevGraph* single, const long long* d_offsets, long long ib, long long ie,
-                 int etype, void* d_edges, long long capacity, bool staged, int block, int grid, cudaStream_t s) {
+void launch_count_range(const DevPlan& P, const DevGraph* single, int* d_counts, bool stage, const SampleRange& r,
+                        int block, int grid, cudaStream_t s) {
+  cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
+  if (stage)
+    launch_sampler<MODE_STAGE, int2>(P, single, r, nullptr, nullptr, 0, d_counts, 0, block, grid, s);
+  else
+    launch_sampler<MODE_COUNT, int2>(P, single, r, nullptr, nullptr, 0, d_counts, 0, block, grid, s);
+}
+
+void launch_emit(const DevPlan& P, const DevGraph* single, const long long* d_offsets, const SampleRange& r,
+                 int etype, void* d_edges, long long capacity, bool staged, int block, int grid, int copy_grid,
+                 cudaStream_t s) {
   cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
   if (staged) {
-    long long chunks = (ie - ib + 31) / 32;
+    long long chunks = (r.ie - r.ib + 31) / 32;
     long long cg = (chunks + 7) / 8;
     int cgrid = (int)(cg < 4096 ? (cg < 1 ? 1 : cg) : 4096);
+    if (copy_grid > 0 && cgrid > copy_grid) cgrid = copy_grid;
     if (etype == CL_E_I32)
-      copy_kernel<int2><<<cgrid, COPY_THREADS, 0, s>>>(P, ib, ie, d_offsets, (int2*)d_edges, capacity);
+      copy_kernel<int2><<<cgrid, COPY_THREADS, 0, s>>>(P, r.ib, r.ie, r.ob, d_offsets, (int2*)d_edges, capacity);
     else
-      copy_kernel<longlong2><<<cgrid, COPY_THREADS, 0, s>>>(P, ib, ie, d_offsets, (longlong2*)d_edges, capacity);
+      copy_kernel<longlong2>
+          <<<cgrid, COPY_THREADS, 0, s>>>(P, r.ib, r.ie, r.ob, d_offsets, (longlong2*)d_edges, capacity);
     // items that outgrew their slots are regenerated (the kernel returns at
     // once when none did)
     cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
   }
   int regen = staged ? 1 : 0;
   if (etype == CL_E_I32)
-    launch_sampler<MODE_EMIT, int2>(P, single, ib, ie, d_offsets, (int2*)d_edges, capacity, nullptr, regen, block,
-                                    grid, s);
+    launch_sampler<MODE_EMIT, int2>(P, single, r, d_offsets, (int2*)d_edges, capacity, nullptr, regen, block, grid, s);
   else
-    launch_sampler<MODE_EMIT, longlong2>(P, single, ib, ie, d_offsets, (longlong2*)d_edges, capacity, nullptr,
-                                         regen, block, grid, s);
+    launch_sampler<MODE_EMIT, longlong2>(P, single, r, d_offsets, (longlong2*)d_edges, capacity, nullptr, regen, block,
+                                         grid, s);
 }
 
 // Per-graph edge offsets of a batch and the capacity status.

@@ -7,6 +7,7 @@ from __future__ import annotations
 import torch
 
 from . import (CL_E_I32, CL_E_I64, CL_W_F64, CL_W_I32, HEAVY_W_DEFAULT, cl_count, cl_emit, cl_generate_batch,
+               cl_generate_host,
                cl_graph, cl_plan_build, cl_plan_create, cl_plan_destroy, cl_plan_graph_info, cl_plan_items,
                cl_plan_scratch_bytes, cl_plan_workspace_bytes, cl_scan, cl_stats, cl_tuning)
 
@@ -87,6 +88,19 @@ class Generator:
         edges = torch.empty((max(m, 1), 2), dtype=dt, device=self.device)
         self.emit(edges, etype)
         return edges[:m]
+
+    def generate_host(self, out: torch.Tensor, etype: int = CL_E_I32, chunks: int = 0, copy_sms: int = 0) -> int:
+        """count + scan + emit with the edges stored straight into `out`, a
+        page-locked (pin_memory) host tensor of (capacity, 2) pairs; returns m.
+        Counting of one item range overlaps the host writes of the previous."""
+        if out.is_cuda or not out.is_pinned():
+            raise ValueError("out must be a page-locked host tensor")
+        want = torch.int32 if etype == CL_E_I32 else torch.int64
+        if out.dtype != want or out.dim() != 2 or out.shape[1] != 2 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (capacity, 2) tensor of the edge type")
+        self.m = cl_generate_host(self.plan, etype, out.data_ptr(), out.shape[0], self.counts, self.offsets, chunks,
+                                  copy_sms, self.stream)
+        return self.m
 
     def generate_batch(self, edges: torch.Tensor, graph_offsets: torch.Tensor, status: torch.Tensor,
                        etype: int = CL_E_I32):
