@@ -257,9 +257,9 @@ def run_ours(args, rank: int, world: int):
             w_dev.copy_(w_host, non_blocking=True)
             pl = P.cl_plan_create([graph2], tun, scratch, sb, sh)
             P.cl_plan_build(pl, ws, wb, sh)
-            # count + scan + emit with the edges stored straight into pinned host memory,
-            # the host writes of one item range overlapping the count of the next
-            mm = P.cl_generate_host(pl, P.CL_E_I32, out_host, cap, counts, offsets, 0, 0, sh)
+            # count + scan + emit by item ranges; each range's host copy (copy engines)
+            # overlaps the sampling of the next
+            mm = P.cl_generate_host(pl, P.CL_E_I32, out_host, cap, edges, counts, offsets, 0, 0, sh)
             P.cl_plan_destroy(pl)
             return mm
 

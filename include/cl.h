@@ -192,25 +192,31 @@ cl_status cl_generate_batch(cl_plan* plan, int32_t etype, void* d_edges, int64_t
                             int64_t* d_graph_offsets, int32_t* d_counts, int64_t* d_offsets,
                             int32_t* d_status, cl_stream_t stream);
 
-/* Count + scan + emit of the whole plan with the edge list written straight
- * into host memory (Algorithm 1's output as in cl_emit, same order and ids).
- * h_edges must be host memory the device can address: page-locked and
- * mapped (cudaHostAlloc, or cudaHostRegister with cudaHostRegisterMapped; on
- * unified-addressing systems every page-locked buffer is mapped), or any host
- * memory where the GPU reads and writes pageable memory (a coherent CPU-GPU
- * link); memory the device cannot address returns CL_ERR_INVALID_ARG.  The items are cut into `chunks` ranges of equal
- * Eq. 3 cost (0: 8; at most CL_HOST_MAX_CHUNKS); while range c + 1 is counted
- * on `stream`, the kernels of range c store its edges to host memory over the
- * host link on a second stream of the plan, on `copy_sms` SMs (0: 16) that the
- * counting launch leaves free.  d_counts (n_items int32) and d_offsets
- * (n_items + 1 int64) are caller device scratch, filled as by cl_count and
- * cl_scan.  Synchronous: returns after the last edge is in host memory, with
- * *h_total = m; m > capacity returns CL_ERR_CAPACITY (ranges that do not fit
- * are not written).  Not capturable in a CUDA graph. */
+/* Count + scan + emit of the whole plan with the edge list delivered to host
+ * memory h_edges (Algorithm 1's output as in cl_emit: same order and ids).
+ * The items are cut into `chunks` ranges of equal Eq. 3 cost (0: 8; at most
+ * CL_HOST_MAX_CHUNKS), and the host transfer of one range overlaps the
+ * sampling of the next:
+ *  - d_edges != NULL (device buffer of `capacity` edges): each range is
+ *    emitted into d_edges at its final offsets, and its host copy is queued
+ *    on the copy engines (a second stream of the plan) while the next range
+ *    is counted; the calling thread waits for each range's total before
+ *    queueing its copy.  h_edges should be page-locked for full speed.
+ *  - d_edges == NULL: the emitting kernels store straight into h_edges, on
+ *    `copy_sms` SMs (0: 16) that the counting launch leaves free.  h_edges
+ *    must then be host memory the device can address: page-locked and mapped
+ *    (cudaHostAlloc; on unified-addressing systems every page-locked buffer
+ *    is mapped), or any host memory where the GPU reads and writes pageable
+ *    memory (a coherent CPU-GPU link); otherwise CL_ERR_INVALID_ARG.
+ * d_counts (n_items int32) and d_offsets (n_items + 1 int64) are caller
+ * device scratch, filled as by cl_count and cl_scan.  Synchronous: returns
+ * after the last edge is in host memory, with *h_total = m; m > capacity
+ * returns CL_ERR_CAPACITY (ranges that do not fit are not written).  Not
+ * capturable in a CUDA graph. */
 #define CL_HOST_MAX_CHUNKS 64
-cl_status cl_generate_host(cl_plan* plan, int32_t etype, void* h_edges, int64_t capacity, int32_t* d_counts,
-                           int64_t* d_offsets, int32_t chunks, int32_t copy_sms, int64_t* h_total,
-                           cl_stream_t stream);
+cl_status cl_generate_host(cl_plan* plan, int32_t etype, void* h_edges, int64_t capacity, void* d_edges,
+                           int32_t* d_counts, int64_t* d_offsets, int32_t chunks, int32_t copy_sms,
+                           int64_t* h_total, cl_stream_t stream);
 
 /* --- expected degrees and weight calibration (Section 3: E[d_i] = w_i - w_i^2/S
  *     without capping; with the cap min(1, .) of Algorithm 1,

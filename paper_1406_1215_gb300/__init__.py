@@ -89,7 +89,7 @@ def load_library(path: str | None = None):
         "cl_scan": ([vp, vp, vp, P(i64), vp], i32),
         "cl_emit": ([vp, vp, i32, vp, i64, i64, i64, vp], i32),
         "cl_generate_batch": ([vp, i32, vp, i64, vp, vp, vp, vp, vp], i32),
-        "cl_generate_host": ([vp, i32, vp, i64, vp, vp, i32, i32, P(i64), vp], i32),
+        "cl_generate_host": ([vp, i32, vp, i64, vp, vp, vp, i32, i32, P(i64), vp], i32),
         "cl_stats": ([vp, P(cl_run_stats), vp], i32),
         "cl_check": ([vp, vp], i32),
         "cl_plan_destroy": ([vp], None),
@@ -206,12 +206,13 @@ def cl_generate_batch(plan, etype: int, d_edges, capacity: int, d_graph_offsets,
     _check(st, "cl_generate_batch")
 
 
-def cl_generate_host(plan, etype: int, h_edges, capacity: int, d_counts, d_offsets, chunks: int = 0,
+def cl_generate_host(plan, etype: int, h_edges, capacity: int, d_edges, d_counts, d_offsets, chunks: int = 0,
                      copy_sms: int = 0, stream=None) -> int:
-    """Whole plan to page-locked host memory (h_edges: pinned tensor or address); returns m."""
+    """Whole plan to host memory (h_edges: pinned tensor or address; d_edges: device
+    staging buffer of the same capacity, or None for direct stores); returns m."""
     m = ctypes.c_int64(0)
-    st = load_library().cl_generate_host(plan, etype, _ptr(h_edges), capacity, _ptr(d_counts), _ptr(d_offsets),
-                                         chunks, copy_sms, ctypes.byref(m), _stream(stream))
+    st = load_library().cl_generate_host(plan, etype, _ptr(h_edges), capacity, _ptr(d_edges), _ptr(d_counts),
+                                         _ptr(d_offsets), chunks, copy_sms, ctypes.byref(m), _stream(stream))
     _check(st, "cl_generate_host")
     return m.value
 

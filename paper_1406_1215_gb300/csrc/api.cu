@@ -58,6 +58,7 @@ struct cl_plan {
   // host-output pipeline (cl_generate_host): a second stream and its events, made on first use
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> events;
+  long long* h_ends = nullptr;  // page-locked, mapped: each chunk's edge total, for its host copy
 };
 
 namespace {
@@ -532,8 +533,8 @@ cl_status cl_check(cl_plan* p, cl_stream_t stream) {
   return (cl_status)err;
 }
 
-cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t capacity, int32_t* d_counts,
-                           int64_t* d_offsets, int32_t chunks, int32_t copy_sms, int64_t* h_total,
+cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t capacity, void* d_edges,
+                           int32_t* d_counts, int64_t* d_offsets, int32_t chunks, int32_t copy_sms, int64_t* h_total,
                            cl_stream_t stream) {
   if (!p || !d_offsets || !h_total || capacity < 0) return CL_ERR_INVALID_ARG;
   if (etype != CL_E_I32 && etype != CL_E_I64) return CL_ERR_INVALID_ARG;
@@ -544,19 +545,21 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   cudaStream_t s = (cudaStream_t)stream;
   cl_status st;
   *h_total = 0;
-  // the kernels store edges through the mapped device address of the host buffer
-  void* d_edges = nullptr;
-  if (capacity > 0 && cudaHostGetDevicePointer(&d_edges, h_edges, 0) != cudaSuccess) {
+  const bool mapped = d_edges == nullptr;  // kernels store into the host buffer itself
+  void* k_edges = d_edges;                 // where the emitting kernels write
+  if (mapped && capacity > 0 && cudaHostGetDevicePointer(&k_edges, h_edges, 0) != cudaSuccess) {
     cudaGetLastError();
-    return CL_ERR_INVALID_ARG;  // not page-locked, device-mapped host memory
+    return CL_ERR_INVALID_ARG;  // host memory the device cannot address
   }
   if ((st = cuda_ok(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s)))) return st;
   if (p->n_items == 0) return cuda_ok(cudaStreamSynchronize(s));
   const int C = chunks == 0 ? 8 : (chunks > p->T ? p->T : chunks);
-  int reserve = copy_sms == 0 ? (p->sms >= 32 ? 16 : p->sms / 2) : copy_sms;
-  if (reserve >= p->sms) reserve = p->sms - 1;
-  if (reserve < 1) reserve = 1;
   if (!p->side && (st = cuda_ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)))) return st;
+  if (!p->h_ends && (st = cuda_ok(cudaHostAlloc((void**)&p->h_ends, (CL_HOST_MAX_CHUNKS + 1) * sizeof(long long),
+                                                cudaHostAllocMapped))))
+    return st;
+  long long* d_ends = nullptr;
+  if ((st = cuda_ok(cudaHostGetDevicePointer((void**)&d_ends, p->h_ends, 0)))) return st;
   while ((int)p->events.size() < C + 1) {
     cudaEvent_t e;
     if ((st = cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)))) return st;
@@ -573,35 +576,65 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   ic[C] = p->n_items;
   const DevGraph* single = p->G == 1 ? &p->dg[0] : nullptr;
   const DevPlan P = dev_plan(p);
-  const int bps = p->grid_count / (p->sms > 0 ? p->sms : 1);
-  const int grid_count = (bps > 0 ? bps : 1) * (p->sms - reserve);
-  const int grid_side = (bps > 0 ? bps : 1) * reserve;
+  const size_t esize = etype == CL_E_I32 ? 8 : 16;
+  const int grid_emit = etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64;
+  // zero-copy path: the counting launch leaves `reserve` SMs to the host stores
+  int reserve = copy_sms == 0 ? (p->sms >= 32 ? 16 : p->sms / 2) : copy_sms;
+  if (reserve >= p->sms) reserve = p->sms - 1;
+  if (reserve < 1) reserve = 1;
+  const int bps = p->grid_count / (p->sms > 0 ? p->sms : 1) > 0 ? p->grid_count / p->sms : 1;
+  const int grid_count = mapped ? bps * (p->sms - reserve) : p->grid_count;
+  const int grid_side = bps * reserve;
   cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s);
   if (p->stage) {
     cudaMemsetAsync(P.overflow, 0, sizeof(int), s);
     cudaMemsetAsync(P.ovf_count, 0, sizeof(unsigned), s);
   }
+  bool over = false;
+  // copy-engine path: once chunk c's edges are in device memory, its host copy is queued on the side stream
+  auto queue_copy = [&](int c) -> cl_status {
+    cl_status r;
+    if ((r = cuda_ok(cudaEventSynchronize(p->events[c])))) return r;
+    const long long start = c == 0 ? 0 : p->h_ends[c - 1], end = p->h_ends[c];
+    if (end > capacity) over = true;
+    if (over || end <= start) return CL_OK;
+    return cuda_ok(cudaMemcpyAsync((char*)h_edges + start * esize, (const char*)d_edges + start * esize,
+                                   (size_t)(end - start) * esize, cudaMemcpyDeviceToHost, p->side));
+  };
   for (int c = 0; c < C; ++c) {
     const long long ib = ic[c], ie = ic[c + 1];
     if (ie > ib) {
       launch_count_range(P, single, d_counts, p->stage, SampleRange{ib, ie, tc[c], ib}, p->block, grid_count, s);
-      if (p->stage)  // the regeneration list as it stands after this chunk's count
+      if (mapped && p->stage)  // the regeneration list as it stands after this chunk's count
         cudaMemcpyAsync(p->d_snap + c, P.ovf_count, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
       launch_count_scan(d_counts + ib, ie - ib, (long long*)d_offsets + ib, p->d_scan_part, s,
                         (const long long*)d_offsets + ib);
     }
     if ((st = last_ok())) return st;
-    cudaEventRecord(p->events[c], s);
-    if (ie == ib) continue;
-    // this chunk's edges go out over the host link while the next chunk is counted
-    cudaStreamWaitEvent(p->side, p->events[c], 0);
-    DevPlan Ps = P;
-    Ps.task_ctr = P.task_ctr + 1;  // its own work counter
-    Ps.ovf_count = p->d_snap + c;
-    launch_emit(Ps, single, (const long long*)d_offsets, SampleRange{ib, ie, tc[c], 0}, etype, d_edges, capacity,
-                p->stage, p->block, grid_side, grid_side, p->side);
+    if (mapped) {
+      // this chunk's edges go out over the host link while the next chunk is counted
+      cudaEventRecord(p->events[c], s);
+      if (ie == ib) continue;
+      cudaStreamWaitEvent(p->side, p->events[c], 0);
+      DevPlan Ps = P;
+      Ps.task_ctr = P.task_ctr + 1;  // its own work counter
+      Ps.ovf_count = p->d_snap + c;
+      launch_emit(Ps, single, (const long long*)d_offsets, SampleRange{ib, ie, tc[c], 0}, etype, k_edges, capacity,
+                  p->stage, p->block, grid_side, grid_side, p->side);
+    } else {
+      if (ie > ib)
+        launch_emit(P, single, (const long long*)d_offsets, SampleRange{ib, ie, tc[c], 0}, etype, d_edges, capacity,
+                    p->stage, p->block, grid_emit, 0, s);
+      // the range's total, stored by a kernel into mapped host memory: a copy-engine
+      // read here would wait behind the large host copies and stall this stream
+      launch_copy_i64((const long long*)d_offsets + ie, d_ends + c, s);
+      cudaEventRecord(p->events[c], s);
+      // the previous chunk is complete on the device by now or soon: queue its host copy
+      if (c > 0 && (st = queue_copy(c - 1))) return st;
+    }
     if ((st = last_ok())) return st;
   }
+  if (!mapped && (st = queue_copy(C - 1))) return st;
   p->staged = p->stage;
   cudaEventRecord(p->events[C], p->side);
   cudaStreamWaitEvent(s, p->events[C], 0);
@@ -621,6 +654,7 @@ void cl_plan_destroy(cl_plan* p) {
     cudaStreamDestroy(p->side);
   }
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->h_ends) cudaFreeHost(p->h_ends);
   delete p;
 }
 

@@ -232,6 +232,7 @@ void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, 
 void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, long long* d_partials,
                        cudaStream_t s, const long long* d_base = nullptr);
 long long scan_partials_needed(long long n);
+void launch_copy_i64(const long long* d_src, long long* dst, cudaStream_t s);
 
 // Items [ib, ie) of a sampling launch; tasks are taken from t0 on (the first
 // task that reaches ib), and edges[0] of an emitting launch holds the first

@@ -564,4 +564,13 @@ void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, l
   count_scan_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_counts, n, d_partials, d_offsets, nt, d_base);
 }
 
+// One int64 from device memory to a (possibly host-mapped) address, by a
+// kernel: unlike a copy-engine transfer it does not queue behind large
+// host copies in flight.
+__global__ void copy_i64_kernel(const long long* __restrict__ src, long long* dst) { *dst = *src; }
+
+void launch_copy_i64(const long long* d_src, long long* dst, cudaStream_t s) {
+  copy_i64_kernel<<<1, 1, 0, s>>>(d_src, dst);
+}
+
 }  // namespace cl

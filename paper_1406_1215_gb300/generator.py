@@ -89,17 +89,24 @@ class Generator:
         self.emit(edges, etype)
         return edges[:m]
 
-    def generate_host(self, out: torch.Tensor, etype: int = CL_E_I32, chunks: int = 0, copy_sms: int = 0) -> int:
-        """count + scan + emit with the edges stored straight into `out`, a
-        page-locked (pin_memory) host tensor of (capacity, 2) pairs; returns m.
-        Counting of one item range overlaps the host writes of the previous."""
-        if out.is_cuda or not out.is_pinned():
-            raise ValueError("out must be a page-locked host tensor")
+    def generate_host(self, out: torch.Tensor, etype: int = CL_E_I32, chunks: int = 0, copy_sms: int = 0,
+                      staging: torch.Tensor | None = None, direct: bool = False) -> int:
+        """count + scan + emit with the edge list delivered into `out`, a host
+        tensor of (capacity, 2) pairs (page-locked for full speed); returns m.
+        The host transfer of one item range overlaps the sampling of the next.
+        staging: device buffer of out's shape for the copy-engine path (made
+        here when omitted); direct=True stores straight into `out` instead."""
+        if out.is_cuda:
+            raise ValueError("out must be a host tensor")
         want = torch.int32 if etype == CL_E_I32 else torch.int64
         if out.dtype != want or out.dim() != 2 or out.shape[1] != 2 or not out.is_contiguous():
             raise ValueError("out must be a contiguous (capacity, 2) tensor of the edge type")
-        self.m = cl_generate_host(self.plan, etype, out.data_ptr(), out.shape[0], self.counts, self.offsets, chunks,
-                                  copy_sms, self.stream)
+        if not direct and staging is None:
+            staging = torch.empty(out.shape, dtype=want, device=self.device)
+        if staging is not None and (staging.shape != out.shape or staging.dtype != want or not staging.is_cuda):
+            raise ValueError("staging must be a device tensor shaped like out")
+        self.m = cl_generate_host(self.plan, etype, out.data_ptr(), out.shape[0], None if direct else staging,
+                                  self.counts, self.offsets, chunks, copy_sms, self.stream)
         return self.m
 
     def generate_batch(self, edges: torch.Tensor, graph_offsets: torch.Tensor, status: torch.Tensor,

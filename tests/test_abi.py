@@ -49,8 +49,8 @@ def test_host_side_argument_checks(L):
     assert L.cl_plan_create(g, 1, None, None, 0, None, ctypes.byref(out)) == 6
     assert L.cl_diag_skip(None, None, None, None, -1, None, None, None) == 1
     m = ctypes.c_int64(5)
-    assert L.cl_generate_host(None, 0, None, 0, None, None, 0, 0, ctypes.byref(m), None) == 1
-    assert L.cl_generate_host(None, 0, None, 0, None, None, 65, 0, ctypes.byref(m), None) == 1
+    assert L.cl_generate_host(None, 0, None, 0, None, None, None, 0, 0, ctypes.byref(m), None) == 1
+    assert L.cl_generate_host(None, 0, None, 0, None, None, None, 65, 0, ctypes.byref(m), None) == 1
     assert L.cl_plan_scratch_bytes(4) > L.cl_plan_scratch_bytes(1) > 0
 
 
