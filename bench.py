@@ -50,9 +50,9 @@ KERNELS_PER_STEP = 18
 # multiplies; an SM issues 32 of them per clock (4 SMSPs x 32 lanes at the half-rate integer
 # multiply, two halves per wide product): 152 SMs x 32 / 20 x 2.07 GHz.
 PHILOX_PEAK = 152 * 32 / 20 * 2.07e9
-# DRAM bytes (read + write) of one staged count launch on this workload, from the one-pass
-# ncu capture summarised in profiles/sample_kernel_stage_pl_n1e8.md; None when stale.
-STAGE_TRAFFIC_BYTES = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one staged count launch on the
+# default workload, from a one-pass ncu capture of this kernel build; None once it has changed.
+STAGE_TRAFFIC_BYTES = 25535473408
 
 
 def peaks():
