@@ -168,20 +168,33 @@ __device__ __forceinline__ ff ff_log_tail(ff s, int e, int J) {
 }
 
 // -ln r for r = A / 2^53, A odd in [1, 2^53) (Tang's reduction with a
-// power-of-two denominator): A' = A 2^e in [2^52, 2^53), J = round(A' / 2^47)
-// in [32, 64], N = A' - J 2^47 in [-2^46, 2^46) (exact as float-float),
-//   -ln r = e ln2 + ln(64/J) - 2 atanh(s),  s = N / (J 2^48 + N).
+// power-of-two denominator and a 513-entry table): A' = A 2^e in [2^52, 2^53),
+// J = round(A' / 2^43) in [512, 1024], N = A' - J 2^43 in [-2^42, 2^42)
+// (exact as float-float),
+//   -ln r = e ln2 + ln(1024/J) - 2 atanh(s),  s = N / (J 2^44 + N),  |s| < 2^-11,
+// so atanh(s) = s + s z (1/3 + z/5), z = s^2, needs float only past s itself
+// (the next term is below 2^-66 |s|).  ln(1024/J) - 2 atanh(s) loses at most
+// one bit to cancellation for J < 1024; J = 1024 has no table term.
 __device__ __forceinline__ ff ff_neglog_r53(unsigned long long A) {
   const int e = __clzll(A) - 11;
   const unsigned long long Ap = A << e;
-  const int J = (int)((Ap + (1ull << 46)) >> 47);
-  const long long N = (long long)Ap - ((long long)J << 47);
-  const ff Nf = ff_from_i47(N);
-  // J 2^48 + N: the first sum is exact (|N| < 2^46 < J 2^48), the second rounds
-  // once, below 2^-47 of the total
-  ff Df = ff_fast_two_sum(__fmul_rn(u23_to_f((unsigned)J), 0x1p48f), Nf.hi);
+  const int J = (int)((Ap + (1ull << 42)) >> 43);
+  const long long N = (long long)Ap - ((long long)J << 43);
+  const unsigned long long a = (unsigned long long)(N < 0 ? -N : N);  // <= 2^42: 21-bit chunks
+  ff Nf = ff_fast_two_sum(__fmul_rn(u23_to_f((unsigned)(a >> 21)), 0x1p21f), u23_to_f((unsigned)a & 0x1FFFFFu));
+  if (N < 0) Nf = ff{-Nf.hi, -Nf.lo};
+  // J 2^44 + N: the first sum is exact (|N| <= 2^42 < J 2^44), the second rounds once,
+  // below 2^-47 of the total
+  ff Df = ff_fast_two_sum(__fmul_rn(u23_to_f((unsigned)J), 0x1p44f), Nf.hi);
   Df.lo = __fadd_rn(Df.lo, Nf.lo);
-  return ff_log_tail(ff_div(Nf, Df), e, J);
+  const ff s = ff_div(Nf, Df);
+  const float z = __fmul_rn(s.hi, s.hi);
+  const float poly = __fmul_rn(z, fmaf(z, 0.2f, 1.0f / 3.0f));
+  const ff at{s.hi, fmaf(s.hi, poly, s.lo)};
+  const float2 t = __ldg(&CL_LNR_FF[J - 512]);
+  const ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f((unsigned)e));
+  const ff r = ff_add_fast(le, ff{t.x, t.y});
+  return ff_add_fast(r, ff{-2.0f * at.hi, -2.0f * at.lo});
 }
 
 // -ln(1 - Q/S) = -ln(A/S), A = S - Q, for integers 0 < Q < S < 2^53; one path

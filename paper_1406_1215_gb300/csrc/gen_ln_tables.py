@@ -1,6 +1,7 @@
 """Writes ln_tables.h: the reduction tables of the logarithms (ln(64/J) for
-J = 32..64, and for J = 65..128 ln(128/J)) and the atanh-series coefficients
-1/(2k+1), split into float-float and double-double pairs.
+J = 32..64, and for J = 65..128 ln(128/J); ln(1024/J) for J = 512..1024) and
+the atanh-series coefficients 1/(2k+1), split into float-float and
+double-double pairs.
 
 Values come from Python's decimal module at 80 significant digits (its ln is
 correctly rounded), so each split is exact to the precision of the pair.
@@ -67,6 +68,12 @@ def main():
         num = 64 if J <= 64 else 128
         hi, lo = split_ff((D(num) / D(J)).ln())
         lines.append(f"  {{{hexf(hi)}f, {hexf(lo)}f}},  // J = {J}")
+    lines.append("};")
+    lines.append("// CL_LNR_FF[J - 512] = ln(1024 / J), J = 512..1024: the finer table of -ln r")
+    lines.append("static __device__ __align__(8) float2 CL_LNR_FF[513] = {")
+    for J in range(512, 1025):
+        hi, lo = split_ff((D(1024) / D(J)).ln())
+        lines.append(f"  {{{hexf(hi)}f, {hexf(lo)}f}},")
     lines.append("};")
     lines.append("static __device__ double CL_LNT_DD[33][2] = {")
     for J in range(32, 65):
