@@ -298,51 +298,41 @@ __device__ __forceinline__ dd dd_neglog_ratio(unsigned long long A, unsigned lon
 // Outcome of one tier: the floor of x clamped at R, or "undecided".
 static constexpr long long SKIP_UNDECIDED = -1;
 
-// floor of 0 <= x < 2^33 as an integer and as a float, from the float's bits
-// (no conversion instructions): below 2^23, x + 2^23 rounded down is
-// 2^23 + floor(x); above, x is an integer whose significand is shifted out.
-__device__ __forceinline__ long long floor_f(float x, float* fl) {
-  if (x < 0x1p23f) {
-    float t = __fadd_rd(x, 0x1p23f);
-    *fl = __fsub_rn(t, 0x1p23f);
-    return (long long)(__float_as_int(t) - 0x4B000000);
-  }
-  *fl = x;
-  unsigned b = __float_as_uint(x);
-  return (long long)((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u);
-}
-
-// x = hi + lo >= 0: floor(x) clamped at R, when x is farther than
-// margin = tau * x from every integer (tau = 2^-40 for float-float).
-// x - k0 (k0 = floor(hi)) is formed exactly; the distances of x to floor(x)
-// and floor(x) + 1 are then each computed with one rounding, so a decision
-// is safe whenever the evaluation error of x is below margin / 2.
+// x = hi + lo >= 0 (a normalized pair, evaluation error below 2^-41 x):
+// floor(x) clamped at R, or SKIP_UNDECIDED when x may lie within tau x =
+// 2^-40 x of an integer.
+//  * hi < 2^23 not an integer: hi is at least ulp(hi) >= 2^-24 hi from every
+//    integer while |lo| <= ulp(hi)/2 and the error is far below that, so
+//    floor(x) = floor(hi) with no window test (the common case);
+//  * hi < 2^23 an integer k: x = k + lo, decided by the sign of lo when
+//    |lo| > tau x;
+//  * 2^23 <= hi < 2^33: hi is an integer and |lo| <= 2^9; floor(x) =
+//    hi + floor(lo), and the fractional part of lo (exact) must be farther than
+//    tau x from 0 and 1.
+// Floors come from the rounded-down sum with 2^23 or 1.5 2^23 (whose ulp is 1)
+// and its bits; no conversion instruction.
 __device__ __forceinline__ long long floor_decide_ff(ff x, long long R) {
-  const float tau = 0x1p-40f;
   if (!(x.hi < 0x1p33f)) return R;  // x >= 2^33 > R for sure
-  float k0f;
-  long long k0 = floor_f(x.hi, &k0f);
-  if (k0 > R) return R;  // x >= R + 1 (1 - 2^-43) > R: the item ends, no window needed
-  ff r = ff_two_sum(__fsub_rn(x.hi, k0f), x.lo);  // x - k0, exact, in (-1/2, 1)
+  const float margin = 0x1p-40f * x.hi;
   long long k;
-  float dlo, dhi;  // distances from x to k and to k + 1
-  if (r.hi < 0.0f) {  // x just below k0 (x.hi integral, x.lo < 0)
-    k = k0 - 1;
-    dhi = __fsub_rn(-r.hi, r.lo);
-    dlo = __fadd_rn(1.0f, r.hi);
-  } else if (r.hi > 1.0f || (r.hi == 1.0f && r.lo >= 0.0f)) {
-    k = k0 + 1;
-    dlo = __fadd_rn(__fsub_rn(r.hi, 1.0f), r.lo);
-    dhi = __fsub_rn(1.0f, dlo);
+  if (x.hi < 0x1p23f) {
+    const float t = __fadd_rd(x.hi, 0x1p23f);  // 2^23 + floor(hi), exact
+    k = (long long)(__float_as_int(t) - 0x4B000000);
+    if (__fsub_rn(t, 0x1p23f) == x.hi) {  // hi is an integer
+      if (x.lo < -margin)
+        k -= 1;
+      else if (!(x.lo > margin))
+        return SKIP_UNDECIDED;
+    }
   } else {
-    k = k0;
-    dlo = __fadd_rn(r.hi, r.lo);
-    dhi = __fsub_rn(__fsub_rn(1.0f, r.hi), r.lo);
+    const unsigned b = __float_as_uint(x.hi);
+    k = (long long)((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u);
+    const float tl = __fadd_rd(x.lo, 12582912.0f);  // 1.5 2^23 + floor(lo), exact for |lo| <= 2^9
+    const float d = __fsub_rn(x.lo, __fsub_rn(tl, 12582912.0f));  // lo - floor(lo) in [0, 1]
+    if (!(d > margin) || !(__fsub_rn(1.0f, d) > margin)) return SKIP_UNDECIDED;
+    k += (long long)(__float_as_int(tl) - 0x4B400000);
   }
-  float margin = tau * x.hi;
-  if (k >= R) return dlo > margin ? R : SKIP_UNDECIDED;  // only x >= R matters
-  if (!(dlo > margin) || !(dhi > margin)) return SKIP_UNDECIDED;
-  return k;
+  return k < R ? k : R;
 }
 
 // Same for double-double with tau = 2^-92 (the tier's evaluation error is below
