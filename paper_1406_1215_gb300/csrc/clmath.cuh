@@ -137,6 +137,18 @@ __device__ __forceinline__ ff ff_from_i47(long long v) {
   return v < 0 ? ff{-r.hi, -r.lo} : r;
 }
 
+// a + b + c for the three terms of a reduced logarithm: a = e ln2 >= 0,
+// b = a table entry in [0, ln2] (so a >= b or a = 0), c = -2 atanh(s) with
+// |c| < a + b unless a + b = 0 (then the result is c): the leading parts sum
+// exactly in two FastTwoSum steps, all trailing parts and errors are added
+// once, one renormalization; the sum loses at most a bit to cancellation.
+__device__ __forceinline__ ff ff_sum3(ff a, ff b, ff c) {
+  const ff h = ff_fast_two_sum(a.hi, b.hi);
+  const ff h2 = ff_fast_two_sum(h.hi, c.hi);
+  const float lo = __fadd_rn(__fadd_rn(h.lo, h2.lo), __fadd_rn(__fadd_rn(a.lo, b.lo), c.lo));
+  return ff_fast_two_sum(h2.hi, lo);
+}
+
 // e ln2 + ln(64/J) - 2 atanh(s) for |s| <= 1/127, J in [32, 128], e >= 1 when
 // J > 64 (then written (e - 1) ln2 + ln(128/J), so both leading terms are
 // non-negative and are added without cancellation; with |2 atanh s| at most
@@ -161,10 +173,8 @@ __device__ __forceinline__ ff ff_log_tail(ff s, int e, int J) {
   ff at = ff_fast_two_sum(s.hi, ch);  // |ch| < 2^-15 |s.hi|
   at.lo = __fadd_rn(at.lo, __fadd_rn(s.lo, cl));
   const float2 t = __ldg(&CL_LNT2_FF[J - 32]);
-  const unsigned e2 = (unsigned)(e - (J > 64 ? 1 : 0));
-  const ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f(e2));
-  const ff r = ff_add_fast(le, ff{t.x, t.y});
-  return ff_add_fast(r, ff{-2.0f * at.hi, -2.0f * at.lo});
+  const ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f((unsigned)(e - (J > 64 ? 1 : 0))));
+  return ff_sum3(le, ff{t.x, t.y}, ff{-2.0f * at.hi, -2.0f * at.lo});
 }
 
 // -ln r for r = A / 2^53, A odd in [1, 2^53) (Tang's reduction with a
@@ -193,8 +203,7 @@ __device__ __forceinline__ ff ff_neglog_r53(unsigned long long A) {
   const ff at{s.hi, fmaf(s.hi, poly, s.lo)};
   const float2 t = __ldg(&CL_LNR_FF[J - 512]);
   const ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f((unsigned)e));
-  const ff r = ff_add_fast(le, ff{t.x, t.y});
-  return ff_add_fast(r, ff{-2.0f * at.hi, -2.0f * at.lo});
+  return ff_sum3(le, ff{t.x, t.y}, ff{-2.0f * at.hi, -2.0f * at.lo});
 }
 
 // -ln(1 - Q/S) = -ln(A/S), A = S - Q, for integers 0 < Q < S < 2^53; one path
@@ -446,13 +455,11 @@ static __device__ __noinline__ long long skip_fallback_dd(unsigned long long Ar,
   return floor_decide_dd(dd_div(Lr, Lp), R, tie);
 }
 
-// -ln(1 - p) for p = Q/S < 2^-12 by its series p (1 + c),
-// c = p/2 + p^2/3 + p^3/4 (the next term, p^4/5, is below 2^-50 p):
-// p = Q (1/S) as float-float (Q exact below 2^46, 1/S to ~2^-48), c as a
-// float pair (p/2 exactly, the rest rounded at ~2^-50), p c with an exact
-// product of the leading parts.
-__device__ __forceinline__ ff ff_neglog1m_small(unsigned long long Q, const LpConst& c) {
-  const ff p = ff_mul(ff_from_u64(Q), ff{c.iS_hi, c.iS_lo});
+// -ln(1 - p) for p < 2^-12 (float-float, relative error ~2^-46) by its series
+// p (1 + c), c = p/2 + p^2/3 + p^3/4 (the next term, p^4/5, is below 2^-50 p):
+// c as a float pair (p/2 exactly, the rest rounded at ~2^-50), p c with an
+// exact product of the leading parts.
+__device__ __forceinline__ ff ff_neglog1m_series(ff p) {
   const float ch = 0.5f * p.hi;
   const float cl = fmaf(p.hi * p.hi, fmaf(p.hi, 0.25f, 1.0f / 3.0f), 0.5f * p.lo);
   ff pc = ff_two_prod(p.hi, ch);
@@ -463,9 +470,10 @@ __device__ __forceinline__ ff ff_neglog1m_small(unsigned long long Q, const LpCo
 }
 
 // -ln(1 - Q/S), 0 < Q < S < 2^53: the series for p < 2^-12 (most candidates
-// of a power-law graph; lanes of a warp mostly agree), the table otherwise.
+// of a power-law graph; lanes of a warp mostly agree), with p = Q (1/S) as
+// float-float (Q exact below 2^46, 1/S to ~2^-48); the table otherwise.
 __device__ __forceinline__ ff ff_neglog1m(unsigned long long Q, unsigned long long S, const LpConst& c) {
-  if (Q < c.Ssmall) return ff_neglog1m_small(Q, c);
+  if (Q < c.Ssmall) return ff_neglog1m_series(ff_mul(ff_from_u64(Q), ff{c.iS_hi, c.iS_lo}));
   return ff_neglog1m_table(Q, S, c);
 }
 
