@@ -407,58 +407,29 @@ void launch_blocks(const DevGraph* d_graphs, int G, long long nblk, unsigned lon
 // with 1/16-edge units so that its prefix is an exact integer.  Costs only
 // schedule work, so single precision is enough for their value (FP64 runs at
 // 1/75 of FP32 here).
-// Approximate conversions for the cost model, built from bit patterns (the
-// conversion instructions run on the slow FP64-class pipe of this GPU):
-// x to float truncated to 24 bits, and x >= 0 to an integer by truncation.
-__device__ __forceinline__ float f_from_u64_trunc(unsigned long long x) {
-  if (x == 0) return 0.0f;
-  const int z = __clzll(x);
-  const unsigned m = (unsigned)((x << z) >> 40);  // leading 24 bits, top bit set
-  return __int_as_float((int)((unsigned)(190 - z) << 23 | (m & 0x7FFFFFu)));
-}
-__device__ __forceinline__ long long ll_from_f_trunc(float x) {  // 0 <= x < 2^62
-  const unsigned b = __float_as_uint(x);
-  const int ex = (int)(b >> 23) - 150;  // x = m 2^ex, m the 24-bit significand
-  const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u;
-  if (ex <= -24) return 0;
-  return ex >= 0 ? (long long)(m << ex) : (long long)(m >> -ex);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __restrict__ gs, int G,
                                                              long long n_items, const T* __restrict__ P,
                                                              long long* __restrict__ C, int* __restrict__ slot,
                                                              int tiny_slots) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  // the warp's first item is located once (bisection over heavy rows); lanes step from it
-  const long long i0 = i - lane;
-  if (i0 >= n_items) return;
-  int g = G == 1 ? 0 : graph_of_item(gs, G, i0);
-  ItemPos ip = item_pos(gs[g], i0 - gs[g].item_begin);
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n_items) return;
-  cursor_advance(gs, g, ip, lane);
+  int g = G == 1 ? 0 : graph_of_item(gs, G, i);
   const DevGraph& gr = gs[g];
-  unsigned j0, end;
-  pos_bounds(gr, ip, j0, end);
-  const T wut = weight_at<T>(gr, ip.u);
-  float wu, dP;
-  if (sizeof(T) == 8 && gr.wtype == CL_W_F64) {  // double weights: the (slow) conversions are rare plans
-    wu = (float)wut;
-    dP = (float)(P[gr.pbase + end] - P[gr.pbase + j0]);
-  } else {
-    wu = f_from_u64_trunc((unsigned long long)(long long)wut);
-    dP = f_from_u64_trunc((unsigned long long)(long long)(P[gr.pbase + end] - P[gr.pbase + j0]));
-  }
+  unsigned u, seg, j0, end;
+  item_bounds(gr, i - gr.item_begin, u, seg, j0, end);
+  float wu = (float)weight_at<T>(gr, u);
+  float dP = (float)(P[gr.pbase + end] - P[gr.pbase + j0]);
   float e = wu * dP * gr.invS_f;  // expected edges of the item (uncapped)
   e = fminf(e, 1e15f);
-  C[i] = 16ll + ll_from_f_trunc(16.0f * e + 0.5f);
+  C[i] = 16ll + (long long)(16.0f * e + 0.5f);
   if (slot) {
     // staging slot: e + 6 sd + 6 entries in whole sectors, at most the item's length
     float want = tiny_slots ? 8.0f : e + 6.0f * sqrtf(e) + 6.0f;
-    want = fminf(want, f_from_u64_trunc(end - j0));
+    float len = (float)(end - j0);
+    want = fminf(want, len);
     want = fminf(want, 1e9f);
-    slot[i] = (int)((ll_from_f_trunc(want) + 8) & ~7ll);
+    slot[i] = ((int)ceilf(want) + 7) & ~7;
   }
 }
 
