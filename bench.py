@@ -169,6 +169,25 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def rank_seed(edge_seed: int, rank: int) -> int:
+    """Replicas: rank r generates its own graph of the same workload with seed edge_seed + r."""
+    return edge_seed + rank
+
+
+def aggregate_ranks(dist, elapsed_s: float, edges: float, device):
+    """Whole-job figures over the ranks: the slowest rank's timed region (max) and
+    the edges every rank generated (sum).  dist = None on one rank."""
+    if dist is None:
+        return elapsed_s, edges
+    import torch
+
+    tt = torch.tensor([elapsed_s], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    mt = torch.tensor([edges], device=device, dtype=torch.float64)
+    dist.all_reduce(mt)
+    return float(tt.item()), float(mt.item())
+
+
 def run_ours(args, rank: int, world: int):
     import torch
 
@@ -188,7 +207,7 @@ def run_ours(args, rank: int, world: int):
         import torch.distributed as dist
 
     w_np, seed = inputs.workload(args.workload)
-    seed = seed + rank
+    seed = rank_seed(seed, rank)
     n = len(w_np)
     w = torch.from_numpy(w_np).to(dev)
     graph = P.cl_graph(n, P.CL_W_I32, w.data_ptr(), seed, 8192.0)
@@ -249,16 +268,7 @@ def run_ours(args, rank: int, world: int):
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    elapsed = t0.elapsed_time(t1) / 1e3
-    if dist:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-        mt = torch.tensor([float(sum(ms))], device=dev, dtype=torch.float64)
-        dist.all_reduce(mt)
-        total_edges = float(mt.item())
-    else:
-        total_edges = float(sum(ms))
+    elapsed, total_edges = aggregate_ranks(dist, t0.elapsed_time(t1) / 1e3, float(sum(ms)), dev)
     value = total_edges / elapsed
     t_emit = statistics.mean(a.elapsed_time(b) for a, b in kern["emit"]) / 1e3
     t_count = statistics.mean(a.elapsed_time(b) for a, b in kern["count"]) / 1e3
