@@ -366,7 +366,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     double cap = em + 6.0 * std::sqrt((double)items * em) + 14.0 * (double)items + 64.0;
     p->pool_cap = (unsigned long long)cap;
   }
-  long long T = (tuning && tuning->tasks > 0) ? tuning->tasks : 16 * warps;
+  long long T = (tuning && tuning->tasks > 0) ? tuning->tasks : 64 * warps;
   long long cap = (items + 31) / 32;
   if (T > cap) T = cap;
   if (T < 1) T = 1;
