@@ -433,6 +433,31 @@ __global__ void __launch_bounds__(COPY_THREADS) copy_kernel(DevPlan P, long long
         uu = ip.u;
       }
     }
+    // items with at least 32 staged edges: the whole warp copies one item at a
+    // time (lane = edge, coalesced, four loads in flight per lane)
+    unsigned big = __ballot_sync(FULL_MASK, cnt >= 32);
+    while (big) {
+      const int l = __ffs(big) - 1;
+      big &= big - 1;
+      const int cl = __shfl_sync(FULL_MASK, cnt, l);
+      const long long ol = __shfl_sync(FULL_MASK, o, l);
+      const long long pl = __shfl_sync(FULL_MASK, pos, l);
+      const unsigned su = __shfl_sync(FULL_MASK, uu, l);
+      for (int e0 = lane; e0 < cl; e0 += 32 * 4) {
+        unsigned v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = e0 + 32 * q < cl ? P.pool[pl + e0 + 32 * q] : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (e0 + 32 * q < cl) {
+            E pr;
+            pr.x = su;
+            pr.y = v[q];
+            edges[ol + e0 + 32 * q] = pr;
+          }
+      }
+    }
+    if (cnt >= 32) cnt = 0;  // done above; the rest are flattened edge by edge
     int incl = cnt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
