@@ -180,6 +180,7 @@ DevPlan dev_plan(const cl_plan* p) {
   P.ovf_count = p->d_ovf_count;
   P.ovf_cap = p->ovf_cap;
   P.wf64 = p->wtype == CL_W_F64 ? 1 : 0;
+  P.pool_cap = p->pool_cap;
   P.blk = p->d_blk;
   return P;
 }
@@ -363,7 +364,9 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
       if (S > 0) em += (S * S - res[g].S2) / (2.0 * S);
     }
     if (em < 0) em = 0;
-    double cap = em + 6.0 * std::sqrt((double)items * em) + 14.0 * (double)items + 64.0;
+    // slots are ceil8(e + 6 sqrt(e) + 6) <= e + 6 sqrt(e) + 13 with e the item's uncapped expected
+    // edges (sum em; Cauchy-Schwarz bounds the square roots); 2^-10 em covers the FP32 costs
+    double cap = em * (1.0 + 0x1p-10) + 6.0 * std::sqrt((double)items * em) + 14.0 * (double)items + 1024.0;
     p->pool_cap = (unsigned long long)cap;
   }
   long long T = (tuning && tuning->tasks > 0) ? tuning->tasks : 64 * warps;

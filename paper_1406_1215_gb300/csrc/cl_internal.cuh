@@ -184,6 +184,7 @@ struct DevPlan {
   int* err;                     // device error word (first error wins)
   unsigned long long* stats;    // iterations, fallbacks, ties
   unsigned* pool;               // staging pool of destination nodes
+  unsigned long long pool_cap;  // its entries: a slot ending past them counts as size 0 (never staged)
   const long long* slot_base;   // per item: first pool entry of its slot (n_items + 1 entries)
   int* overflow;                // set when an item outgrew its slot
   long long* ovf_list;          // items that outgrew their slot (first ovf_cap of them)
@@ -192,6 +193,13 @@ struct DevPlan {
   int wf64;                     // the plan's weights are doubles
   const unsigned long long* blk;  // integer weights: uniform-block table (BLK_MIXED or (w << 32) | run end)
 };
+
+// Staging slot of item i in entries (0: the item is never staged, its slot
+// would end past the pool).
+__device__ __forceinline__ unsigned slot_size(const DevPlan& P, long long i) {
+  const long long b = P.slot_base[i + 1];
+  return (unsigned long long)b <= P.pool_cap ? (unsigned)(b - P.slot_base[i]) : 0u;
+}
 
 // Weight of node v of a graph with weights W and uniform-block offset bbase:
 // from the lane's cached run (v < run_end), else from the block table, else

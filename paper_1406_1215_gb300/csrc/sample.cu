@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
           else
             cursor_advance(P.graphs, gi_l, ip, rank);
           if (MODE == MODE_EMIT && regen_only &&
-              offsets[item + 1] - offsets[item] <= P.slot_base[item + 1] - P.slot_base[item])
+              offsets[item + 1] - offsets[item] <= (long long)slot_size(P, item))
             have = fresh = false;  // staged: the copy kernel wrote it
         }
         u = ip.u;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       if (MODE == MODE_EMIT) obase = offsets[item] - off_base;
       if (MODE == MODE_STAGE) {
         sbase = P.slot_base[item];
-        ssize = (unsigned)(P.slot_base[item + 1] - sbase);
+        ssize = slot_size(P, item);
       }
       target = j0;  // first position: p = Q(j0) / S
       look = true;
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(COPY_THREADS) copy_kernel(DevPlan P, long long
       o = offsets[i] - off_base;
       long long cc = offsets[i + 1] - offsets[i];
       pos = P.slot_base[i];
-      if (cc <= P.slot_base[i + 1] - pos) cnt = (int)cc;  // else: not staged, regenerated
+      if (cc <= (long long)slot_size(P, i)) cnt = (int)cc;  // else: not staged, regenerated
       if (cnt > 0) {
         int gi = g0;
         ItemPos ip = p0;
