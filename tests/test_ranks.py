@@ -1,5 +1,5 @@
-"""The multi-rank path of bench.py on CPU: world size 2 over gloo (each GPU machine
-here has one GPU, so ranks are replicas).  The whole-job figures are the
+"""The multi-rank path of bench.py on CPU: world size 2 over gloo (ranks are
+replicas: each generates its own graph).  The whole-job figures are the
 slowest rank's timed region and the sum of every rank's edges; each rank draws
 its own graph; a rank that raises ends the job without hanging the other."""
 import os
