@@ -366,10 +366,17 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       } else {
         counts[item] = (int)k;
         if (MODE == MODE_STAGE) {
-          if (k <= ssize) {  // the item's last partial group
-            unsigned c = k & (GROUP - 1);
-            unsigned long long base = sbase + (k & ~(GROUP - 1));
-            for (unsigned i = 0; i < c; ++i) P.pool[base + i] = sgrp[i][threadIdx.x];
+          if (k <= ssize) {
+            // the item's last partial group, written as a whole sector (the slot is a
+            // multiple of 8 entries, so the group lies inside it; entries past k are
+            // never read): no read-modify-write of a partial sector, no per-entry loop
+            if (k & (GROUP - 1)) {
+              uint4* dst = (uint4*)(P.pool + sbase + (k & ~(GROUP - 1)));
+              dst[0] = make_uint4(sgrp[0][threadIdx.x], sgrp[1][threadIdx.x], sgrp[2][threadIdx.x],
+                                  sgrp[3][threadIdx.x]);
+              dst[1] = make_uint4(sgrp[4][threadIdx.x], sgrp[5][threadIdx.x], sgrp[6][threadIdx.x],
+                                  sgrp[7][threadIdx.x]);
+            }
           } else {  // remember it for the regeneration pass
             unsigned idx = atomicAdd(P.ovf_count, 1u);
             if (idx < P.ovf_cap) P.ovf_list[idx] = item;
