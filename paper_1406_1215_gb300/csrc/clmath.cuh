@@ -471,9 +471,12 @@ __device__ __forceinline__ ff ff_neglog1m_series(ff p) {
 
 // -ln(1 - Q/S), 0 < Q < S < 2^53: the series for p < 2^-12 (most candidates
 // of a power-law graph; lanes of a warp mostly agree), with p = Q (1/S) as
-// float-float (Q exact below 2^46, 1/S to ~2^-48); the table otherwise.
+// float-float (Q exact, 1/S to ~2^-48); the table otherwise.
 __device__ __forceinline__ ff ff_neglog1m(unsigned long long Q, unsigned long long S, const LpConst& c) {
-  if (Q < c.Ssmall) return ff_neglog1m_series(ff_mul(ff_from_u64(Q), ff{c.iS_hi, c.iS_lo}));
+  if (Q < c.Ssmall) {  // Q < S / 4096 < 2^41: two exact 23-bit chunks
+    const ff q = ff_fast_two_sum(u23_to_f_2p23((unsigned)(Q >> 23)), u23_to_f((unsigned)Q & 0x7FFFFFu));
+    return ff_neglog1m_series(ff_mul(q, ff{c.iS_hi, c.iS_lo}));
+  }
   return ff_neglog1m_table(Q, S, c);
 }
 
