@@ -180,6 +180,14 @@ cl_status cl_scan(cl_plan* plan, const int32_t* d_counts, int64_t* d_offsets, in
 cl_status cl_emit(cl_plan* plan, const int64_t* d_offsets, int32_t etype, void* d_edges, int64_t capacity,
                   int64_t item_begin, int64_t item_end, cl_stream_t stream);
 
+/* cl_count + cl_scan + cl_emit over all items in one call, with no host
+ * round trip: d_counts and d_offsets are filled as by cl_count and cl_scan,
+ * edge k of item i goes to d_edges[d_offsets[i] + k].  h_total (nullable):
+ * synchronizes and returns m; m > capacity returns CL_ERR_CAPACITY (nothing is
+ * written to d_edges then).  Asynchronous when h_total is NULL. */
+cl_status cl_generate(cl_plan* plan, int32_t etype, void* d_edges, int64_t capacity, int32_t* d_counts,
+                      int64_t* d_offsets, int64_t* h_total, cl_stream_t stream);
+
 /* Count + scan + emit for every graph of the plan, with no host round trip:
  * graph g's edges start at d_graph_offsets[g] (G + 1 int64 entries,
  * d_graph_offsets[G] = total edges) and carry the graph's local vertex ids.

@@ -89,6 +89,7 @@ def load_library(path: str | None = None):
         "cl_scan": ([vp, vp, vp, P(i64), vp], i32),
         "cl_emit": ([vp, vp, i32, vp, i64, i64, i64, vp], i32),
         "cl_generate_batch": ([vp, i32, vp, i64, vp, vp, vp, vp, vp], i32),
+        "cl_generate": ([vp, i32, vp, i64, vp, vp, vp, vp], i32),
         "cl_generate_host": ([vp, i32, vp, i64, vp, vp, vp, i32, i32, P(i64), vp], i32),
         "cl_stats": ([vp, P(cl_run_stats), vp], i32),
         "cl_check": ([vp, vp], i32),
@@ -204,6 +205,16 @@ def cl_generate_batch(plan, etype: int, d_edges, capacity: int, d_graph_offsets,
     st = load_library().cl_generate_batch(plan, etype, _ptr(d_edges), capacity, _ptr(d_graph_offsets),
                                           _ptr(d_counts), _ptr(d_offsets), _ptr(d_status), _stream(stream))
     _check(st, "cl_generate_batch")
+
+
+def cl_generate(plan, etype: int, d_edges, capacity: int, d_counts, d_offsets, want_total: bool = True,
+                stream=None):
+    """count + scan + emit in one call; returns m when want_total (synchronizes), else None."""
+    m = ctypes.c_int64(0)
+    st = load_library().cl_generate(plan, etype, _ptr(d_edges), capacity, _ptr(d_counts), _ptr(d_offsets),
+                                    ctypes.byref(m) if want_total else None, _stream(stream))
+    _check(st, "cl_generate")
+    return m.value if want_total else None
 
 
 def cl_generate_host(plan, etype: int, h_edges, capacity: int, d_edges, d_counts, d_offsets, chunks: int = 0,

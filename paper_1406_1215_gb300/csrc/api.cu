@@ -484,6 +484,28 @@ cl_status cl_emit(cl_plan* p, const int64_t* d_offsets, int32_t etype, void* d_e
   return last_ok();
 }
 
+cl_status cl_generate(cl_plan* p, int32_t etype, void* d_edges, int64_t capacity, int32_t* d_counts,
+                      int64_t* d_offsets, int64_t* h_total, cl_stream_t stream) {
+  if (!p || !d_offsets || capacity < 0) return CL_ERR_INVALID_ARG;
+  if (etype != CL_E_I32 && etype != CL_E_I64) return CL_ERR_INVALID_ARG;
+  if (p->n_items > 0 && !d_counts) return CL_ERR_INVALID_ARG;
+  if (capacity > 0 && !d_edges) return CL_ERR_INVALID_ARG;
+  if (!p->built) return CL_ERR_STATE;
+  cl_status st;
+  if ((st = cl_count(p, d_counts, stream))) return st;
+  if ((st = cl_scan(p, d_counts, d_offsets, nullptr, stream))) return st;
+  if (p->n_items > 0 && (st = cl_emit(p, d_offsets, etype, d_edges, capacity, 0, p->n_items, stream))) return st;
+  if (!h_total) return CL_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int err = 0;
+  if ((st = cuda_ok(cudaMemcpyAsync(h_total, d_offsets + p->n_items, sizeof(int64_t), cudaMemcpyDeviceToHost, s))))
+    return st;
+  if ((st = cuda_ok(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)))) return st;
+  if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
+  if (*h_total > capacity) return CL_ERR_CAPACITY;
+  return err ? (cl_status)err : CL_OK;
+}
+
 cl_status cl_generate_batch(cl_plan* p, int32_t etype, void* d_edges, int64_t capacity, int64_t* d_graph_offsets,
                             int32_t* d_counts, int64_t* d_offsets, int32_t* d_status, cl_stream_t stream) {
   if (!p || !d_graph_offsets || !d_offsets || !d_status || capacity < 0) return CL_ERR_INVALID_ARG;

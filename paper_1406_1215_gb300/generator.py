@@ -6,8 +6,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (CL_E_I32, CL_E_I64, CL_W_F64, CL_W_I32, HEAVY_W_DEFAULT, cl_count, cl_emit, cl_generate_batch,
-               cl_generate_host,
+from . import (CL_E_I32, CL_E_I64, CL_W_F64, CL_W_I32, HEAVY_W_DEFAULT, cl_count, cl_emit, cl_generate,
+               cl_generate_batch, cl_generate_host,
                cl_graph, cl_plan_build, cl_plan_create, cl_plan_destroy, cl_plan_graph_info, cl_plan_items,
                cl_plan_scratch_bytes, cl_plan_workspace_bytes, cl_scan, cl_stats, cl_tuning)
 
@@ -88,6 +88,13 @@ class Generator:
         edges = torch.empty((max(m, 1), 2), dtype=dt, device=self.device)
         self.emit(edges, etype)
         return edges[:m]
+
+    def generate_into(self, edges: torch.Tensor, etype: int = CL_E_I32) -> int:
+        """count + scan + emit in one library call into `edges` (a device (capacity, 2)
+        tensor); returns m."""
+        cap = edges.shape[0] if edges.numel() else 0
+        self.m = cl_generate(self.plan, etype, edges, cap, self.counts, self.offsets, True, self.stream)
+        return self.m
 
     def generate_host(self, out: torch.Tensor, etype: int = CL_E_I32, chunks: int = 0, copy_sms: int = 0,
                       staging: torch.Tensor | None = None, direct: bool = False) -> int:
