@@ -54,21 +54,6 @@ __device__ __forceinline__ ff ff_two_prod(float a, float b) {
   float p = __fmul_rn(a, b);
   return {p, fmaf(a, b, -p)};
 }
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
-  ff s = ff_two_sum(x.hi, y.hi);
-  ff t = ff_two_sum(x.lo, y.lo);
-  s.lo = __fadd_rn(s.lo, t.hi);
-  s = ff_fast_two_sum(s.hi, s.lo);
-  s.lo = __fadd_rn(s.lo, t.lo);
-  return ff_fast_two_sum(s.hi, s.lo);
-}
-// Dekker's add: error <= ~2^-47 (|x| + |y|); used where |x + y| >= (|x| + |y|) / 4
-__device__ __forceinline__ ff ff_add_fast(ff x, ff y) {
-  ff s = ff_two_sum(x.hi, y.hi);
-  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
-  return ff_fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ ff ff_mul(ff x, ff y) {
   ff p = ff_two_prod(x.hi, y.hi);
   p.lo = fmaf(x.hi, y.lo, p.lo);
@@ -128,12 +113,6 @@ __device__ __forceinline__ ff ff_from_u64(unsigned long long x) {
 }
 __device__ __forceinline__ ff ff_from_i64(long long v) {
   ff r = ff_from_u64((unsigned long long)(v < 0 ? -v : v));
-  return v < 0 ? ff{-r.hi, -r.lo} : r;
-}
-// |v| <= 2^46, exactly: two 23-bit chunks.
-__device__ __forceinline__ ff ff_from_i47(long long v) {
-  const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
-  ff r = ff_fast_two_sum(__fmul_rn(u23_to_f((unsigned)(a >> 23)), 0x1p23f), u23_to_f((unsigned)a & 0x7FFFFFu));
   return v < 0 ? ff{-r.hi, -r.lo} : r;
 }
 
