@@ -139,7 +139,8 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
 cl_status cl_plan_workspace_bytes(const cl_plan* plan, size_t* bytes);
 
 /* Builds the equal-cost task split of Eq. 3 in the workspace: per item
- * c = 1 + (w_u / S) * sum_{v in item} w_v (Eq. 1-2; Eq. 6 for light rows),
+ * c = c0 + (w_u / S) * sum_{v in item} w_v (Eq. 1-2; Eq. 6 for light rows;
+ * c0 = 4, the measured work of an item apart from its edges, where Eq. 1 has 1),
  * C = inclusive prefix of c (Calc-Cost of Algorithm 2 as a device-wide scan),
  * task t starts at the first item with C >= t * Zbar, Zbar = C_total / tasks
  * (Eq. 3; found as the items where floor(C / Zbar) changes, the rule of

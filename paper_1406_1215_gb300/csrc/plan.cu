@@ -402,11 +402,16 @@ void launch_blocks(const DevGraph* d_graphs, int G, long long nblk, unsigned lon
 }
 
 // --------------------------------------------------------------- costs, Eq. 3
-// c_i = 1 + (w_u / S) * sum_{v in [j0, end)} w_v  (Eq. 1-2; for a light row
-// [u+1, n) this is Eq. 6: (w_u / S)(S - sigma_u - w_u) + 1), in fixed point
-// with 1/16-edge units so that its prefix is an exact integer.  Costs only
-// schedule work, so single precision is enough for their value (FP64 runs at
-// 1/75 of FP32 here).
+// c_i = c0 + (w_u / S) * sum_{v in [j0, end)} w_v  (Eq. 1-2; for a light row
+// [u+1, n) this is Eq. 6: (w_u / S)(S - sigma_u - w_u) + c0), in fixed point
+// with 1/16-edge units so that its prefix is an exact integer.  The constant
+// term is the work of an item apart from its edges; Eq. 1 counts it as 1, but
+// here an item's set-up and end (bounds, first weight and L_p, the lane refill,
+// the count and the staging flush) cost about as much as 4 loop iterations, so
+// c0 = 4: tasks of equal cost then take equal time whether they hold a few long
+// items or many short ones.  Costs only schedule work, so single precision is
+// enough for their value (FP64 runs at 1/75 of FP32 here).
+constexpr long long ITEM_COST_16 = 64;  // c0 = 4 edges, in 1/16-edge units
 template <typename T>
 __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __restrict__ gs, int G,
                                                              long long n_items, const T* __restrict__ P,
@@ -422,7 +427,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __r
   float dP = (float)(P[gr.pbase + end] - P[gr.pbase + j0]);
   float e = wu * dP * gr.invS_f;  // expected edges of the item (uncapped)
   e = fminf(e, 1e15f);
-  C[i] = 16ll + (long long)(16.0f * e + 0.5f);
+  C[i] = ITEM_COST_16 + (long long)(16.0f * e + 0.5f);
   if (slot) {
     // staging slot: e + 6 sd + 6 entries in whole sectors, at most the item's length
     float want = tiny_slots ? 8.0f : e + 6.0f * sqrtf(e) + 6.0f;
