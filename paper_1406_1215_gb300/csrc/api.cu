@@ -57,6 +57,7 @@ struct cl_plan {
   unsigned* d_snap = nullptr;  // per-chunk snapshots of the regeneration list length
   // host-output pipeline (cl_generate_host): a second stream and its events, made on first use
   cudaStream_t side = nullptr;
+  cudaStream_t aux = nullptr;  // counts the second range beside the first
   std::vector<cudaEvent_t> events;
   long long* h_ends = nullptr;  // page-locked, mapped: each chunk's edge total, for its host copy
 };
@@ -580,12 +581,13 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   if (p->n_items == 0) return cuda_ok(cudaStreamSynchronize(s));
   const int C = chunks == 0 ? 8 : (chunks > p->T ? p->T : chunks);
   if (!p->side && (st = cuda_ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)))) return st;
+  if (!p->aux && (st = cuda_ok(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking)))) return st;
   if (!p->h_ends && (st = cuda_ok(cudaHostAlloc((void**)&p->h_ends, (CL_HOST_MAX_CHUNKS + 1) * sizeof(long long),
                                                 cudaHostAllocMapped))))
     return st;
   long long* d_ends = nullptr;
   if ((st = cuda_ok(cudaHostGetDevicePointer((void**)&d_ends, p->h_ends, 0)))) return st;
-  while ((int)p->events.size() < C + 1) {
+  while ((int)p->events.size() < C + 3) {
     cudaEvent_t e;
     if ((st = cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)))) return st;
     p->events.push_back(e);
@@ -600,7 +602,25 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
   ic[C] = p->n_items;
   const DevGraph* single = p->G == 1 ? &p->dg[0] : nullptr;
-  const DevPlan P = dev_plan(p);
+  // The first two ranges are counted side by side, each on half of the counting
+  // grid: the heaviest items (the first segments of the heaviest rows) bound a
+  // range's count from below by their serial length, and the first host copy
+  // waits for them; counted one after the other, the second range's heavy items
+  // would start only once the first range is done.  The second range (stream
+  // aux) keeps its own task counter and regeneration list.
+  const bool lead = C >= 2;
+  DevPlan P = dev_plan(p);
+  DevPlan Pa = P;
+  if (lead) {
+    Pa.task_ctr = P.task_ctr + 2;
+    if (p->stage) {
+      const unsigned half = P.ovf_cap / 2;
+      Pa.ovf_count = P.ovf_count + 1;
+      Pa.ovf_list = P.ovf_list + (P.ovf_cap - half);
+      Pa.ovf_cap = half;
+      P.ovf_cap -= half;
+    }
+  }
   const size_t esize = etype == CL_E_I32 ? 8 : 16;
   const int grid_emit = etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64;
   // zero-copy path: the counting launch leaves `reserve` SMs to the host stores
@@ -613,7 +633,18 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s);
   if (p->stage) {
     cudaMemsetAsync(P.overflow, 0, sizeof(int), s);
-    cudaMemsetAsync(P.ovf_count, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(P.ovf_count, 0, 2 * sizeof(unsigned), s);
+  }
+  if (lead) {
+    cudaEventRecord(p->events[C + 1], s);  // the resets above, before the aux stream's count
+    cudaStreamWaitEvent(p->aux, p->events[C + 1], 0);
+    const int gh = grid_count / 2 > 0 ? grid_count / 2 : 1;
+    if (ic[0] < ic[1])
+      launch_count_range(P, single, d_counts, p->stage, SampleRange{ic[0], ic[1], tc[0], ic[0]}, p->block, gh, s);
+    if (ic[1] < ic[2])
+      launch_count_range(Pa, single, d_counts, p->stage, SampleRange{ic[1], ic[2], tc[1], ic[1]}, p->block,
+                         grid_count - gh, p->aux);
+    cudaEventRecord(p->events[C + 2], p->aux);
   }
   bool over = false;
   // copy-engine path: once chunk c's edges are in device memory, its host copy is queued on the side stream
@@ -628,10 +659,19 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   };
   for (int c = 0; c < C; ++c) {
     const long long ib = ic[c], ie = ic[c + 1];
+    if (lead && c == 1) cudaStreamWaitEvent(s, p->events[C + 2], 0);  // the aux stream's count
+    // the plan view of this range's count and emit: its regeneration list
+    DevPlan Pc = P;
+    if (lead && c == 1) {
+      Pc.ovf_list = Pa.ovf_list;
+      Pc.ovf_count = Pa.ovf_count;
+      Pc.ovf_cap = Pa.ovf_cap;
+    }
     if (ie > ib) {
-      launch_count_range(P, single, d_counts, p->stage, SampleRange{ib, ie, tc[c], ib}, p->block, grid_count, s);
+      if (!(lead && c < 2))
+        launch_count_range(P, single, d_counts, p->stage, SampleRange{ib, ie, tc[c], ib}, p->block, grid_count, s);
       if (mapped && p->stage)  // the regeneration list as it stands after this chunk's count
-        cudaMemcpyAsync(p->d_snap + c, P.ovf_count, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(p->d_snap + c, Pc.ovf_count, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
       launch_count_scan(d_counts + ib, ie - ib, (long long*)d_offsets + ib, p->d_scan_part, s,
                         (const long long*)d_offsets + ib);
     }
@@ -641,14 +681,14 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
       cudaEventRecord(p->events[c], s);
       if (ie == ib) continue;
       cudaStreamWaitEvent(p->side, p->events[c], 0);
-      DevPlan Ps = P;
+      DevPlan Ps = Pc;
       Ps.task_ctr = P.task_ctr + 1;  // its own work counter
       Ps.ovf_count = p->d_snap + c;
       launch_emit(Ps, single, (const long long*)d_offsets, SampleRange{ib, ie, tc[c], 0}, etype, k_edges, capacity,
                   p->stage, p->block, grid_side, grid_side, p->side);
     } else {
       if (ie > ib)
-        launch_emit(P, single, (const long long*)d_offsets, SampleRange{ib, ie, tc[c], 0}, etype, d_edges, capacity,
+        launch_emit(Pc, single, (const long long*)d_offsets, SampleRange{ib, ie, tc[c], 0}, etype, d_edges, capacity,
                     p->stage, p->block, grid_emit, 0, s);
       // the range's total, stored by a kernel into mapped host memory: a copy-engine
       // read here would wait behind the large host copies and stall this stream
@@ -677,6 +717,10 @@ void cl_plan_destroy(cl_plan* p) {
   if (p->side) {
     cudaStreamSynchronize(p->side);
     cudaStreamDestroy(p->side);
+  }
+  if (p->aux) {
+    cudaStreamSynchronize(p->aux);
+    cudaStreamDestroy(p->aux);
   }
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   if (p->h_ends) cudaFreeHost(p->h_ends);
