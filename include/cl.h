@@ -93,7 +93,13 @@ typedef struct {
                           * items that outgrow their slot are regenerated by cl_emit */
   double stage_factor;   /* 0; a negative value shrinks every slot to 8 entries, so that most
                           * items take the regeneration path (for testing that path) */
+  int32_t partition;     /* task split: CL_PART_UCP (0, default) = equal Eq. 1 cost per task
+                          * (Eq. 3, the uniform cost partition); CL_PART_CP (1) = equal node counts
+                          * (the paper's consecutive partition, Section 4), for comparing the two;
+                          * other values: CL_ERR_INVALID_ARG */
 } cl_tuning;
+
+enum { CL_PART_UCP = 0, CL_PART_CP = 1 };
 
 typedef struct {
   int64_t n, H;           /* nodes, heavy rows */

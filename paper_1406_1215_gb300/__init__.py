@@ -25,6 +25,7 @@ STATUS_NAMES = {
  CL_ERR_TIMEOUT, CL_ERR_CUDA, CL_ERR_STATE, CL_ERR_DEVICE) = range(1, 11)
 CL_W_I32, CL_W_F64 = 0, 1
 CL_E_I32, CL_E_I64 = 0, 1
+CL_PART_UCP, CL_PART_CP = 0, 1
 HEAVY_W_DEFAULT = 8192.0
 
 
@@ -41,7 +42,7 @@ class cl_graph(ctypes.Structure):
 
 class cl_tuning(ctypes.Structure):
     _fields_ = [("tasks", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("no_stage", ctypes.c_int32), ("stage_factor", ctypes.c_double)]
+                ("no_stage", ctypes.c_int32), ("stage_factor", ctypes.c_double), ("partition", ctypes.c_int32)]
 
 
 class cl_graph_info(ctypes.Structure):

@@ -33,6 +33,7 @@ struct cl_plan {
   unsigned long long pool_cap = 0;    // staging pool entries
   bool staged = false;                // the last cl_count staged (cl_emit copies)
   bool tiny_slots = false;            // testing knob: 8-entry slots (most items regenerate)
+  int partition = CL_PART_UCP;        // task split: Eq. 3 (default) or the consecutive partition
   unsigned ovf_cap = 1;               // regeneration list entries
   // workspace (after cl_plan_build)
   bool built = false;
@@ -357,6 +358,11 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
   // Cauchy-Schwarz sum_i sqrt(e_i) <= sqrt(items * sum_i e_i), so this bounds the pool
   p->stage = !(tuning && tuning->no_stage);
   p->tiny_slots = tuning && tuning->stage_factor < 0;
+  p->partition = tuning ? tuning->partition : CL_PART_UCP;
+  if (p->partition != CL_PART_UCP && p->partition != CL_PART_CP) {
+    delete p;
+    return CL_ERR_INVALID_ARG;
+  }
   p->ovf_cap = (unsigned)(items < (long long)OVF_CAP ? (items > 0 ? items : 1) : OVF_CAP);
   if (p->stage) {
     double em = 0;
@@ -424,8 +430,10 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   const bool f64 = p->wtype == CL_W_F64;
   launch_weight_prefix(L.graphs, L.tile_begin, p->G, p->ntiles, f64, L.P, L.part, s);
   if (!f64) launch_blocks(L.graphs, p->G, p->csize, L.blk, s);
+  long long n_nodes = 0;
+  for (int g = 0; g < p->G; ++g) n_nodes += p->dg[g].n;
   launch_costs_and_tasks(L.graphs, p->G, p->n_items, f64, L.P, L.C, L.part, L.task, p->T, L.slot32,
-                         p->tiny_slots ? 1 : 0, s);
+                         p->tiny_slots ? 1 : 0, p->partition, n_nodes, s);
   if (p->stage) launch_count_scan(L.slot32, p->n_items, L.slot_base, L.scan_part, s);  // slot bases
   if ((st = last_ok())) return st;
   p->built = true;

@@ -233,7 +233,7 @@ void launch_blocks(const DevGraph* d_graphs, int G, long long nblk, unsigned lon
 // task boundaries of Eq. 3; when d_slot32 is given, also every item's staging slot size.
 void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, bool f64, const void* d_P,
                             long long* d_C, long long* d_partials, long long* d_task_start, int T, int* d_slot32,
-                            int tiny_slots, cudaStream_t s);
+                            int tiny_slots, int partition, long long n_nodes, cudaStream_t s);
 // Exclusive int32 -> int64 scan with the total at out[n]; with d_base, every
 // output is offset by *d_base (read on the device: a scan of a later range of
 // items continues from the total of the earlier ones, with no host round trip).

@@ -497,11 +497,41 @@ __global__ void task_bounds_kernel(const long long* __restrict__ C, long long n_
   task_start[t] = lo;
 }
 
+// The paper's consecutive partition (CP, Section 4), kept for comparison with
+// Eq. 3: task t takes the rows [t N / T, (t+1) N / T) of the plan's N nodes
+// (graphs concatenated), i.e. the items from the first item of row t N / T on.
+// Tasks only schedule work, so the output is the same as under Eq. 3.
+__global__ void cp_bounds_kernel(const DevGraph* __restrict__ gs, int G, long long n_nodes, long long n_items,
+                                 long long* __restrict__ task_start, int T) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t > T) return;
+  if (t == T) {
+    task_start[T] = n_items;
+    return;
+  }
+  const long long N = (long long)((unsigned __int128)(unsigned long long)t * (unsigned long long)n_nodes /
+                                  (unsigned long long)T);
+  // graph g holds the nodes [pbase_g - g, pbase_g - g + n_g): its prefix has n_g + 1 entries
+  int lo = 0, hi = G - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (gs[mid].pbase - mid <= N)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const DevGraph& g = gs[lo];
+  const long long u = N - (g.pbase - lo);
+  long long first = u < g.Hh ? heavy_items_before(u, g.n) : g.n_heavy + (u > g.H ? u - g.H : 0);
+  if (first > g.n_items) first = g.n_items;
+  task_start[t] = g.item_begin + first;
+}
+
 long long scan_partials_needed(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, bool f64, const void* d_P,
                             long long* d_C, long long* d_partials, long long* d_task_start, int T, int* d_slot32,
-                            int tiny_slots, cudaStream_t s) {
+                            int tiny_slots, int partition, long long n_nodes, cudaStream_t s) {
   if (n_items <= 0) {
     // empty plan: a single empty task
     cudaMemsetAsync(d_task_start, 0, 2 * sizeof(long long), s);
@@ -518,7 +548,10 @@ void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, 
   tile_reduce_i64_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
   partials_scan_kernel<long long><<<1, 1024, 0, s>>>(d_partials, nt, nullptr);
   tile_incl_scan_i64_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
-  task_bounds_kernel<<<(T + 1 + 255) / 256, 256, 0, s>>>(d_C, n_items, d_task_start, T);
+  if (partition == CL_PART_CP)
+    cp_bounds_kernel<<<(T + 1 + 255) / 256, 256, 0, s>>>(d_graphs, G, n_nodes, n_items, d_task_start, T);
+  else
+    task_bounds_kernel<<<(T + 1 + 255) / 256, 256, 0, s>>>(d_C, n_items, d_task_start, T);
 }
 
 // --------------------------------------------------------------- count scan

@@ -25,7 +25,8 @@ class Generator:
     GPU, one seed each) with its workspace and count / offset buffers."""
 
     def __init__(self, weights, seeds, heavy_w: float = HEAVY_W_DEFAULT, tasks: int = 0, block: int = 0,
-                 blocks_per_sm: int = 0, no_stage: int = 0, stage_factor: float = 0.0, stream=None):
+                 blocks_per_sm: int = 0, no_stage: int = 0, stage_factor: float = 0.0, partition: int = 0,
+                 stream=None):
         if isinstance(weights, torch.Tensor):
             weights = [weights]
             seeds = [seeds]
@@ -41,7 +42,7 @@ class Generator:
         self.stream = stream
         graphs = [cl_graph(w.numel(), _wtype(w), w.data_ptr(), s & (2**64 - 1), float(heavy_w))
                   for w, s in zip(self.weights, self.seeds)]
-        tun = cl_tuning(tasks, block, blocks_per_sm, no_stage, stage_factor)
+        tun = cl_tuning(tasks, block, blocks_per_sm, no_stage, stage_factor, partition)
         sb = cl_plan_scratch_bytes(self.G)
         scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
         self.plan = cl_plan_create(graphs, tun, scratch, sb, stream)

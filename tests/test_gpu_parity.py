@@ -106,7 +106,8 @@ def test_output_independent_of_tuning():
     w = inputs.powerlaw_degrees(60000, 2.3, 2, 2000, 23)
     ref, cref, _ = gpu_generate(w, 3, heavy_w=500.0)
     for tun in ({"tasks": 1}, {"tasks": 7}, {"tasks": 100000}, {"block": 32}, {"block": 128, "blocks_per_sm": 1},
-                {"blocks_per_sm": 2, "tasks": 333}, {"no_stage": 1},
+                {"blocks_per_sm": 2, "tasks": 333}, {"no_stage": 1}, {"partition": 1},
+                {"partition": 1, "tasks": 333},  # the paper's consecutive partition instead of Eq. 3
                 {"stage_factor": -1.0}):  # 8-entry slots: most items regenerated by cl_emit
         E, c, _ = gpu_generate(w, 3, heavy_w=500.0, **tun)
         assert np.array_equal(c, cref), tun
