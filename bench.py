@@ -141,7 +141,7 @@ def cpu_baseline(w: np.ndarray, seed: int, budget_s: float = 24.0, cores: int | 
     edges = sum(r[0] for r in res)
     ranges = sum(r[2] for r in res)
     rate = sum(r[0] / r[1] for r in res)  # the processes run at the same time
-    return {"value": rate, "unit": "edges/s", "cores": cores, "kind": "oracle",
+    return {"value": rate, "unit": "edges/s", "cores": cores, "kind": "oracle", "per_core": rate / cores,
             "sample": f"{cores} processes x {per:.1f} s: {ranges} random ranges of 2000 consecutive items "
                       f"({edges} edges) of the same workload, count pass of the oracle"}
 
@@ -235,9 +235,11 @@ def run_ours(args, rank: int, world: int):
     edges = torch.empty((cap, 2), dtype=torch.int32, device=dev)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    kern = {"count": [], "emit": []}
+    kern = {"count": [], "emit": [], "plan": [], "step": []}
 
     def step(timed_kernels: bool):
+        p0 = ev()
+        p0.record(stream)
         pl = P.cl_plan_create([graph], tun, scratch, sb, sh)
         P.cl_plan_build(pl, ws, wb, sh)
         e0, e1, e2, e3 = ev(), ev(), ev(), ev()
@@ -251,6 +253,8 @@ def run_ours(args, rank: int, world: int):
         if timed_kernels:
             kern["count"].append((e0, e1))
             kern["emit"].append((e2, e3))
+            kern["plan"].append((p0, e0))  # validation, S, prefixes, Eq. 1 costs, Eq. 3 tasks
+            kern["step"].append((p0, e3))
         err = P.cl_check(pl, sh)
         P.cl_plan_destroy(pl)
         if err != 0:
@@ -276,6 +280,8 @@ def run_ours(args, rank: int, world: int):
     value = total_edges / elapsed
     t_emit = statistics.mean(a.elapsed_time(b) for a, b in kern["emit"]) / 1e3
     t_count = statistics.mean(a.elapsed_time(b) for a, b in kern["count"]) / 1e3
+    t_plan = statistics.mean(a.elapsed_time(b) for a, b in kern["plan"]) / 1e3
+    step_each = [a.elapsed_time(b) for a, b in kern["step"]]
     m_step = ms[-1]
     peak, how = peaks()
     step_s = elapsed / args.steps
@@ -334,7 +340,8 @@ def run_ours(args, rank: int, world: int):
         "hbm_write_roofline": {"achieved": 8.0 * m_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
                                "frac": 8.0 * m_step / step_s / 1e9 / peak, "peak_source": how,
                                "algorithmic_bytes": "8 B per edge (int32 pair) per step"},
-        "kernel_ms": {"count": t_count * 1e3, "emit": t_emit * 1e3},
+        "kernel_ms": {"count": t_count * 1e3, "emit": t_emit * 1e3, "plan": t_plan * 1e3},
+        "step_ms": {"median": statistics.median(step_each), "best": min(step_each)},
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
