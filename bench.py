@@ -306,16 +306,33 @@ def run_ours(args, rank: int, world: int):
             P.cl_plan_destroy(pl)
             return mm
 
+        def link_gbps():
+            # device -> pinned host rate of a plain 4 GB copy: the floor of this leg, which
+            # varies between boxes and runs (the host side is shared)
+            k = min(cap, 1 << 29)
+            x, y = ev(), ev()
+            x.record(stream)
+            out_host[:k].copy_(edges[:k], non_blocking=True)
+            y.record(stream)
+            torch.cuda.synchronize()
+            return 8 * k / (x.elapsed_time(y) / 1e3) / 1e9
+
         e2e_step()
         torch.cuda.synchronize()
-        a, b = ev(), ev()
-        a.record(stream)
-        em = [e2e_step() for _ in range(e_steps)]
-        b.record(stream)
+        link0 = link_gbps()
+        marks = [ev() for _ in range(e_steps + 1)]
+        marks[0].record(stream)
+        em = []
+        for i in range(e_steps):
+            em.append(e2e_step())
+            marks[i + 1].record(stream)
         torch.cuda.synchronize()
-        et = a.elapsed_time(b) / 1e3
+        et = marks[0].elapsed_time(marks[-1]) / 1e3
+        link1 = link_gbps()
         e2e = {"value": sum(em) / et, "unit": "edges/s", "h2d_bytes_per_step": 4 * n,
-               "d2h_bytes_per_step": 8 * em[-1], "steps": e_steps}
+               "d2h_bytes_per_step": 8 * em[-1], "steps": e_steps,
+               "step_ms": [marks[i].elapsed_time(marks[i + 1]) for i in range(e_steps)],
+               "link_d2h_gbps": [link0, link1]}
         del out_host, w_host
 
     # free the main leg's buffers (tens of GB) before the other legs
