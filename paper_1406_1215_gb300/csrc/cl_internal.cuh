@@ -107,6 +107,28 @@ __device__ __forceinline__ ItemPos item_pos(const DevGraph& g, long long local) 
   return ItemPos{local, (unsigned)lo, (unsigned)k};
 }
 
+// Same as item_pos, for the per-item plan kernels: rows u with u + 1 < 2^16
+// all have the K0 = N1 + 1 segments 0 .. N1, so an item among their
+// K0 * min(Hh, 2^16 - 1) items is row local / K0, segment local % K0 (a float
+// quotient corrected to the exact one) with no bisection.  (The samplers keep
+// item_pos: they call it once per task, and the extra code costs registers.)
+__device__ __forceinline__ ItemPos item_pos_direct(const DevGraph& g, long long local) {
+  const long long K0 = ((g.n - 1) >> SEG_LOG2) + 1;
+  const long long U0 = g.Hh < (1ll << SEG_LOG2) - 1 ? g.Hh : (1ll << SEG_LOG2) - 1;
+  if (local >= U0 * K0) return item_pos(g, local);
+  long long u = (long long)__fmul_rz((float)local, __frcp_rn((float)K0));
+  long long r = local - u * K0;
+  while (r < 0) {
+    --u;
+    r += K0;
+  }
+  while (r >= K0) {
+    ++u;
+    r -= K0;
+  }
+  return ItemPos{local, (unsigned)u, (unsigned)r};
+}
+
 // The position d >= 0 items after p (p.local + d an item of g): segments
 // advance within the row, and a step past the row's last segment moves to the
 // first segment of the next row -- one loop turn per row crossed.
@@ -139,7 +161,7 @@ __device__ __forceinline__ void pos_bounds(const DevGraph& g, ItemPos p, unsigne
 // Bounds of a graph's local item: source row u, segment field, [j0, end).
 __device__ __forceinline__ void item_bounds(const DevGraph& g, long long local, unsigned& u, unsigned& seg,
                                             unsigned& j0, unsigned& end) {
-  const ItemPos p = item_pos(g, local);
+  const ItemPos p = item_pos_direct(g, local);
   u = p.u;
   seg = p.seg;
   pos_bounds(g, p, j0, end);
