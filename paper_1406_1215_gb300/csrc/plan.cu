@@ -463,10 +463,18 @@ __global__ void __launch_bounds__(PLAN_THREADS) tile_incl_scan_i64_kernel(long l
   }
   long long tot;
   long long run = block_excl_scan(loc, &tot) + part[blockIdx.x];
+  __shared__ long long res[SCAN_TILE + PLAN_THREADS];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
     run += v[k];
-    if (i0 + k < n) x[i0 + k] = run;
+    res[threadIdx.x * (SCAN_ITEMS + 1) + k] = run;
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x * (long long)SCAN_TILE;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int q = k * PLAN_THREADS + threadIdx.x;
+    if (t0 + q < n) x[t0 + q] = res[q + q / SCAN_ITEMS];
   }
 }
 
@@ -582,10 +590,20 @@ __global__ void __launch_bounds__(PLAN_THREADS) count_scan_kernel(const int* __r
   }
   long long tot;
   long long run = block_excl_scan(loc, &tot) + part[blockIdx.x] + b0;
+  // results staged in shared memory (one pad word per thread's 8: 2-way bank
+  // access) and written out coalesced
+  __shared__ long long res[SCAN_TILE + PLAN_THREADS];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    if (i0 + k < n) out[i0 + k] = run;
+    res[threadIdx.x * (SCAN_ITEMS + 1) + k] = run;
     run += v[k];
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x * (long long)SCAN_TILE;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int q = k * PLAN_THREADS + threadIdx.x;
+    if (t0 + q < n) out[t0 + q] = res[q + q / SCAN_ITEMS];
   }
   if (blockIdx.x == nt - 1 && threadIdx.x == 0) out[n] = part[blockIdx.x] + tot + b0;
 }
