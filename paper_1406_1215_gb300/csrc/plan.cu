@@ -178,15 +178,20 @@ __global__ void __launch_bounds__(PLAN_THREADS) analyze_kernel(const DevGraph* _
       if (hi) atomicAdd(&gb[1], hi);
     }
   } else {
+    // integers only in the loop (int <-> double conversions run at the FP64 rate here):
+    // x >= hw  <=>  x >= ceil(hw) for an integer x; squares summed exactly in 128 bits
+    const long long hwi = hw <= 0.0 ? 0 : (hw > 4294967296.0 ? (1ll << 33) : (long long)ceil(hw));
     const int* w = (const int*)gr.w;
+    unsigned __int128 sq_i = 0;
     for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       int x = w[i];
       if (x < 0) flags |= 2u;
       if (i + 1 < n && x < w[i + 1]) flags |= 1u;
-      if ((double)x >= hw) ++heavy;
+      if ((long long)x >= hwi) ++heavy;
       sum += (unsigned long long)(long long)x;
-      sq += (double)x * (double)x;
+      sq_i += (unsigned long long)((long long)x * (long long)x);
     }
+    sq = (double)(unsigned long long)(sq_i >> 64) * 18446744073709551616.0 + (double)(unsigned long long)sq_i;
   }
   // block reductions
   unsigned long long s = block_reduce(sum);
@@ -412,6 +417,29 @@ void launch_blocks(const DevGraph* d_graphs, int G, long long nblk, unsigned lon
 // items or many short ones.  Costs only schedule work, so single precision is
 // enough for their value (FP64 runs at 1/75 of FP32 here).
 constexpr long long ITEM_COST_16 = 64;  // c0 = 4 edges, in 1/16-edge units
+
+// Integer <-> float conversions run on the FP64-class pipe of this GPU (1/75 of
+// the FP32 rate); the per-item plan kernels build them from bit patterns
+// instead (for 0 <= x < 2^16 the float with bits 0x4B000000 | x is 2^23 + x).
+__device__ __forceinline__ float u16_to_f(unsigned x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
+// float(x), correctly rounded
+__device__ __forceinline__ float u32_to_f(unsigned x) { return fmaf(u16_to_f(x >> 16), 65536.0f, u16_to_f(x & 0xFFFFu)); }
+// float(v) for 0 <= v < 2^64 to within an ulp
+__device__ __forceinline__ float u64_to_f(unsigned long long v) {
+  return fmaf(u32_to_f((unsigned)(v >> 32)), 4294967296.0f, u32_to_f((unsigned)v));
+}
+// floor(f) for 0 <= f < 2^62
+__device__ __forceinline__ long long f_floor_to_ll(float f) {
+  if (f < 8388608.0f) return (long long)(__float_as_int(__fadd_rd(f, 8388608.0f)) - 0x4B000000);
+  const unsigned b = __float_as_uint(f);  // an integer: the significand shifted left
+  return (long long)((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u);
+}
+// ceil(f) for 0 <= f < 2^30
+__device__ __forceinline__ int f_ceil_to_i(float f) {
+  if (f < 8388608.0f) return __float_as_int(__fadd_ru(f, 8388608.0f)) - 0x4B000000;
+  const unsigned b = __float_as_uint(f);
+  return (int)(((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u));
+}
 template <typename T>
 __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __restrict__ gs, int G,
                                                              long long n_items, const T* __restrict__ P,
@@ -423,18 +451,26 @@ __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __r
   const DevGraph& gr = gs[g];
   unsigned u, seg, j0, end;
   item_bounds(gr, i - gr.item_begin, u, seg, j0, end);
-  float wu = (float)weight_at<T>(gr, u);
-  float dP = (float)(P[gr.pbase + end] - P[gr.pbase + j0]);
+  constexpr bool ints = T(1) / T(2) == T(0);  // integer weights, int64 prefix
+  float wu, dP, len;
+  if (ints) {
+    wu = u32_to_f((unsigned)((const int*)gr.w)[u]);
+    dP = u64_to_f((unsigned long long)(P[gr.pbase + end] - P[gr.pbase + j0]));
+    len = u32_to_f(end - j0);
+  } else {
+    wu = (float)weight_at<T>(gr, u);
+    dP = (float)(P[gr.pbase + end] - P[gr.pbase + j0]);
+    len = (float)(end - j0);
+  }
   float e = wu * dP * gr.invS_f;  // expected edges of the item (uncapped)
   e = fminf(e, 1e15f);
-  C[i] = ITEM_COST_16 + (long long)(16.0f * e + 0.5f);
+  C[i] = ITEM_COST_16 + f_floor_to_ll(16.0f * e + 0.5f);
   if (slot) {
     // staging slot: e + 6 sd + 6 entries in whole sectors, at most the item's length
     float want = tiny_slots ? 8.0f : e + 6.0f * sqrtf(e) + 6.0f;
-    float len = (float)(end - j0);
     want = fminf(want, len);
     want = fminf(want, 1e9f);
-    slot[i] = ((int)ceilf(want) + 7) & ~7;
+    slot[i] = (f_ceil_to_i(want) + 7) & ~7;
   }
 }
 
