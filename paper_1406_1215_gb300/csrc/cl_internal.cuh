@@ -107,6 +107,29 @@ __device__ __forceinline__ ItemPos item_pos(const DevGraph& g, long long local) 
   return ItemPos{local, (unsigned)lo, (unsigned)k};
 }
 
+// Integer <-> float conversions run on the FP64-class pipe of this GPU (1/75 of
+// the FP32 rate); the per-item plan kernels build them from bit patterns
+// instead (for 0 <= x < 2^16 the float with bits 0x4B000000 | x is 2^23 + x).
+__device__ __forceinline__ float u16_to_f(unsigned x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
+// float(x), correctly rounded
+__device__ __forceinline__ float u32_to_f(unsigned x) { return fmaf(u16_to_f(x >> 16), 65536.0f, u16_to_f(x & 0xFFFFu)); }
+// float(v) for 0 <= v < 2^64 to within an ulp
+__device__ __forceinline__ float u64_to_f(unsigned long long v) {
+  return fmaf(u32_to_f((unsigned)(v >> 32)), 4294967296.0f, u32_to_f((unsigned)v));
+}
+// floor(f) for 0 <= f < 2^62
+__device__ __forceinline__ long long f_floor_to_ll(float f) {
+  if (f < 8388608.0f) return (long long)(__float_as_int(__fadd_rd(f, 8388608.0f)) - 0x4B000000);
+  const unsigned b = __float_as_uint(f);  // an integer: the significand shifted left
+  return (long long)((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u);
+}
+// ceil(f) for 0 <= f < 2^30
+__device__ __forceinline__ int f_ceil_to_i(float f) {
+  if (f < 8388608.0f) return __float_as_int(__fadd_ru(f, 8388608.0f)) - 0x4B000000;
+  const unsigned b = __float_as_uint(f);
+  return (int)(((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u));
+}
+
 // Same as item_pos, for the per-item plan kernels: rows u with u + 1 < 2^16
 // all have the K0 = N1 + 1 segments 0 .. N1, so an item among their
 // K0 * min(Hh, 2^16 - 1) items is row local / K0, segment local % K0 (a float
@@ -116,7 +139,7 @@ __device__ __forceinline__ ItemPos item_pos_direct(const DevGraph& g, long long 
   const long long K0 = ((g.n - 1) >> SEG_LOG2) + 1;
   const long long U0 = g.Hh < (1ll << SEG_LOG2) - 1 ? g.Hh : (1ll << SEG_LOG2) - 1;
   if (local >= U0 * K0) return item_pos(g, local);
-  long long u = (long long)__fmul_rz((float)local, __frcp_rn((float)K0));
+  long long u = f_floor_to_ll(__fmul_rz(u64_to_f((unsigned long long)local), __frcp_rn(u32_to_f((unsigned)K0))));
   long long r = local - u * K0;
   while (r < 0) {
     --u;

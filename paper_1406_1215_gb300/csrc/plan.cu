@@ -338,10 +338,18 @@ __global__ void __launch_bounds__(PLAN_THREADS) wprefix_scan_kernel(const DevGra
   }
   T tot;
   T ex = block_excl_scan(loc, &tot) + part[t];
+  // staged in shared memory (one pad word per thread's 8) and written out coalesced
+  __shared__ T res[SCAN_TILE + PLAN_THREADS];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    if (u0 + k < len) P[gr.pbase + u0 + k] = ex;
+    res[threadIdx.x * (SCAN_ITEMS + 1) + k] = ex;
     ex += v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int q = k * PLAN_THREADS + threadIdx.x;
+    if (e0 + q < len) P[gr.pbase + e0 + q] = res[q + q / SCAN_ITEMS];
   }
 }
 
@@ -418,28 +426,6 @@ void launch_blocks(const DevGraph* d_graphs, int G, long long nblk, unsigned lon
 // enough for their value (FP64 runs at 1/75 of FP32 here).
 constexpr long long ITEM_COST_16 = 64;  // c0 = 4 edges, in 1/16-edge units
 
-// Integer <-> float conversions run on the FP64-class pipe of this GPU (1/75 of
-// the FP32 rate); the per-item plan kernels build them from bit patterns
-// instead (for 0 <= x < 2^16 the float with bits 0x4B000000 | x is 2^23 + x).
-__device__ __forceinline__ float u16_to_f(unsigned x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
-// float(x), correctly rounded
-__device__ __forceinline__ float u32_to_f(unsigned x) { return fmaf(u16_to_f(x >> 16), 65536.0f, u16_to_f(x & 0xFFFFu)); }
-// float(v) for 0 <= v < 2^64 to within an ulp
-__device__ __forceinline__ float u64_to_f(unsigned long long v) {
-  return fmaf(u32_to_f((unsigned)(v >> 32)), 4294967296.0f, u32_to_f((unsigned)v));
-}
-// floor(f) for 0 <= f < 2^62
-__device__ __forceinline__ long long f_floor_to_ll(float f) {
-  if (f < 8388608.0f) return (long long)(__float_as_int(__fadd_rd(f, 8388608.0f)) - 0x4B000000);
-  const unsigned b = __float_as_uint(f);  // an integer: the significand shifted left
-  return (long long)((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u);
-}
-// ceil(f) for 0 <= f < 2^30
-__device__ __forceinline__ int f_ceil_to_i(float f) {
-  if (f < 8388608.0f) return __float_as_int(__fadd_ru(f, 8388608.0f)) - 0x4B000000;
-  const unsigned b = __float_as_uint(f);
-  return (int)(((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u));
-}
 template <typename T>
 __global__ void __launch_bounds__(PLAN_THREADS) costs_kernel(const DevGraph* __restrict__ gs, int G,
                                                              long long n_items, const T* __restrict__ P,
