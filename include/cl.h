@@ -211,7 +211,8 @@ cl_status cl_generate_batch(cl_plan* plan, int32_t etype, void* d_edges, int64_t
  * memory h_edges (Algorithm 1's output as in cl_emit: same order and ids).
  * The items are cut into `chunks` ranges of equal Eq. 3 cost (0: 8; at most
  * CL_HOST_MAX_CHUNKS), and the host transfer of one range overlaps the
- * sampling of the next:
+ * sampling of the next (the first two ranges, which hold the heaviest rows,
+ * are counted side by side on a third stream of the plan):
  *  - d_edges != NULL (device buffer of `capacity` edges): each range is
  *    emitted into d_edges at its final offsets, and its host copy is queued
  *    on the copy engines (a second stream of the plan) while the next range
