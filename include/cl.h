@@ -83,7 +83,8 @@ typedef struct {
 
 /* Performance knobs only: no choice changes any output bit. */
 typedef struct {
-  int32_t tasks;         /* number of equal-cost tasks (Eq. 3 partitions); 0 = automatic */
+  int32_t tasks;         /* number of equal-cost tasks (Eq. 3 partitions); 0 = automatic: about
+                          * 10^4 edges of cost each, 4 to 64 per resident warp of the count pass */
   int32_t block;         /* threads per block of the sampler kernels, multiple of 32, <= 256; 0 = 256 */
   int32_t blocks_per_sm; /* resident blocks per SM for the persistent sampler grid; 0 = automatic */
   int32_t no_stage;      /* 1: cl_count only counts and cl_emit regenerates every item (smaller

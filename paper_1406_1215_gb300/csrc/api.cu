@@ -364,19 +364,30 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     return CL_ERR_INVALID_ARG;
   }
   p->ovf_cap = (unsigned)(items < (long long)OVF_CAP ? (items > 0 ? items : 1) : OVF_CAP);
+  double em = 0;  // uncapped expected edges of the plan
+  for (int g = 0; g < G; ++g) {
+    double S = p->dg[g].S_d;
+    if (S > 0) em += (S * S - res[g].S2) / (2.0 * S);
+  }
+  if (em < 0) em = 0;
   if (p->stage) {
-    double em = 0;
-    for (int g = 0; g < G; ++g) {
-      double S = p->dg[g].S_d;
-      if (S > 0) em += (S * S - res[g].S2) / (2.0 * S);
-    }
-    if (em < 0) em = 0;
     // slots are ceil8(e + 6 sqrt(e) + 6) <= e + 6 sqrt(e) + 13 with e the item's uncapped expected
     // edges (sum em; Cauchy-Schwarz bounds the square roots); 2^-10 em covers the FP32 costs
     double cap = em * (1.0 + 0x1p-10) + 6.0 * std::sqrt((double)items * em) + 14.0 * (double)items + 1024.0;
     p->pool_cap = (unsigned long long)cap;
   }
-  long long T = (tuning && tuning->tasks > 0) ? tuning->tasks : 64 * warps;
+  // default task count: tasks of about 10^4 edges of cost (Eq. 1 with the per-item
+  // constant 4), between 4 and 64 per resident warp -- fewer, larger tasks cost less
+  // to hand out on small graphs (n = 10^7: 9.6 against 10.5 ms per count pass), and
+  // 64 per warp keeps the end of a large pass short
+  long long T = 64 * warps;
+  if (tuning && tuning->tasks > 0) {
+    T = tuning->tasks;
+  } else {
+    double want = (em + 4.0 * (double)items) / 1e4;
+    if (want < 4.0 * (double)warps) want = 4.0 * (double)warps;
+    if (want < (double)T) T = (long long)want;
+  }
   long long cap = (items + 31) / 32;
   if (T > cap) T = cap;
   if (T < 1) T = 1;
