@@ -64,13 +64,15 @@ def test_generate_double_weights():
     assert np.array_equal(one_call(w, 4), oracle_edges(w, 4))
 
 
-def test_generate_batch_matches_singles():
+@pytest.mark.parametrize("partition", [0, 1])
+def test_generate_batch_matches_singles(partition):
+    # partition 1: the consecutive partition over the graphs' concatenated nodes
     lib()
     from paper_1406_1215_gb300.generator import Generator
 
     ws = [inputs.powerlaw_degrees(n, 2.4, 2, max(3, int(n ** 0.5)), 60 + n % 7) for n in (1000, 20000, 3, 70000, 1)]
     seeds = [5, 6, 7, 8, 9]
-    g = Generator([cuda(w) for w in ws], seeds)
+    g = Generator([cuda(w) for w in ws], seeds, partition=partition, tasks=0 if partition == 0 else 37)
     m3 = g.generate().shape[0]
     edges = torch.empty((m3, 2), dtype=torch.int32, device="cuda")
     assert g.generate_into(edges) == m3
