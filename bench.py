@@ -351,7 +351,8 @@ def run_ours(args, rank: int, world: int):
         "config": dict(WORKLOADS[args.workload], **COMMON),
         "edges_per_step": m_step,
         "roofline": {"bound": "alu", "achieved": alu, "peak": PHILOX_PEAK, "unit": "Philox blocks/s",
-                     "frac": alu / PHILOX_PEAK, "traffic": STAGE_TRAFFIC_BYTES,
+                     "frac": alu / PHILOX_PEAK,
+                     "traffic": STAGE_TRAFFIC_BYTES if args.workload == "pl_n1e8" else None,
                      "kernel": "sample_kernel<STAGE> (staged count pass)", "iterations_per_launch": iterations,
                      "peak_source": "derived from SM count, integer-multiply issue rate and max clock"},
         "hbm_write_roofline": {"achieved": 8.0 * m_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
