@@ -255,3 +255,33 @@ def test_regeneration_beyond_the_overflow_list():
     for a in rng.integers(0, o.n_items - 20, 10):
         off = np.concatenate([[0], np.cumsum(cref.astype(np.int64))])
         assert np.array_equal(E[off[a]:off[a + 20]], o.generate(int(a), int(a) + 20))
+
+
+def test_table1_er_network():
+    """The paper's Table 1 ER row (1M nodes, 200M edges; tests/golden/table1_er.json):
+    the edge count within 6 sd of the oracle's exact E[m], and sampled items equal to
+    the oracle's."""
+    import json
+    import os
+
+    lib()
+    from paper_1406_1215_gb300.generator import Generator
+
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_er.json")))
+    n = gold["nodes"]
+    w = inputs.constant_weights(n, round(2 * gold["edges"] / n))
+    N, S, var = oracle.expected_edges_i32(w)
+    g = Generator(cuda(w), 17)
+    E = g.generate()
+    m = E.shape[0]
+    off = g.offsets.cpu().numpy()
+    g.close()
+    assert abs(m - N / S) < 6 * math.sqrt(var)
+    assert abs(m - gold["edges"]) <= gold["edges_rounding"] + 6 * math.sqrt(var)
+    og = oracle.Graph(w, 17)
+    rng = np.random.default_rng(3)
+    Eh = None
+    for a in [0, og.n_items - 20] + [int(x) for x in rng.integers(0, og.n_items - 20, 20)]:
+        if Eh is None:
+            Eh = E.cpu().numpy().astype(np.int64)
+        assert np.array_equal(Eh[int(off[a]):int(off[a + 20])], og.generate(a, a + 20)), a
