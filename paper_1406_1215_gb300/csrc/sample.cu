@@ -398,11 +398,14 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
   }
 }
 
-// ---- copy of staged destinations.  A warp takes 32 consecutive items; their
-// edges form one contiguous output range, which the lanes cover edge by edge
-// (consecutive lanes write consecutive pairs); each lane finds its edge's item
-// by a 5-step search over the warp's inclusive count prefix, so every load is
-// independent of the others.
+// ---- copy of staged destinations.  A warp takes 32 consecutive items (one
+// per lane, pulled from a counter); their edges form one contiguous output
+// range.  Items with at least 32 staged edges are copied by the whole warp, one
+// item at a time (lane = edge); the others are flattened: the lanes cover their
+// edges edge by edge (consecutive lanes write consecutive pairs), each lane
+// finding its edge's item by a 5-step search over the warp's inclusive count
+// prefix, so every load is independent of the others.  A memory-latency-bound
+// kernel: 8 resident blocks per SM keep the loads in flight.
 constexpr int COPY_THREADS = 256;
 
 template <typename E>
