@@ -23,6 +23,9 @@
  *     recorded in a device error word and reported by the next synchronizing
  *     call (cl_check, cl_stats, cl_scan with a non-null h_total).  No kernel
  *     traps, asserts or waits on another block.
+ *   - CL_ERR_CUDA after a launch comes from the runtime's last-error state,
+ *     read (and cleared) right after the launch: it can also report an error
+ *     that earlier, unrelated CUDA work left pending on the calling thread.
  *   - vertex ids are positions in the sorted order; relabelling is the
  *     caller's job.
  *
@@ -293,9 +296,10 @@ void cl_plan_destroy(cl_plan* plan);
  * plan or workspace and without allocating: its scratch (one int64 per 2048
  * counts) is a fixed 1 MiB array inside the library, held on every GPU that
  * loads the library until the process exits.  n must be <= 2^28
- * (268,435,456); larger n returns CL_ERR_RANGE.  The first call on each
- * device looks up that array's device address with the device current; make
- * that first call before any stream capture.  All calls share the one array
+ * (268,435,456); larger n returns CL_ERR_RANGE.  Every call looks up that
+ * array's device address on the current device (so a cudaDeviceReset between
+ * calls is harmless); the first call on a device also loads the library's
+ * device code there, so make it before any stream capture.  All calls share the one array
  * (its contents are rewritten by each call, nothing needs clearing), so two
  * calls that may run at the same time on the GPU -- on different streams, or
  * from different host threads -- race and corrupt each other's result:

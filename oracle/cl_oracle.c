@@ -226,10 +226,9 @@ int32_t or_item_bounds(const or_graph* g, const or_info* info, int64_t item, int
   return 0;
 }
 
-/* Q(u, v) = min(w_u w_v, S): the numerator of p_{u,v} = min(w_u w_v / S, 1) of
- * Section 3 and line "q <- min(w_i w_v / S, 1)" of Algorithm 1.  Integer
- * weights: exact 64-bit product.  Double weights: the rounded product,
- * capped iff it is >= S. */
+/* Q(u, v) = min(w_u w_v, S): S times the pair probability min(w_u w_v / S, 1)
+ * of Section 3.  Integer weights: exact 64-bit product.  Double weights: the
+ * rounded product, capped iff it is >= S. */
 static double Qof(const or_graph* g, const or_info* info, int64_t u, int64_t v) {
   if (g->wtype == OR_W_I32) {
     const int32_t* w = (const int32_t*)g->w;
@@ -254,9 +253,16 @@ static int accept(const or_graph* g, uint32_t lo, uint32_t hi, double Qprev, dou
   return fma(r, Qprev, -Qv) < 0.0; /* the sign of a fused multiply-add is exact */
 }
 
-/* Create-Edges of Algorithm 1 for one item: the while loop over the candidates
- * of row u in [j0, end), with the reading that a candidate at or past `end`
- * ends the item. */
+/* One item of the skip sampler (Section 3, Algorithm 1).  In a
+ * non-increasing weight sequence the pair probability of row u only falls as
+ * v grows, so the probability p_ref = Q_ref / S of the last visited position
+ * bounds every later one: the next candidate is found by a geometric skip
+ * drawn at p_ref (Section 3's skip length), and a candidate v is kept with
+ * probability Q(u, v) / Q_ref (thinning), which leaves every pair of the item
+ * an edge with probability Q(u, v) / S, independently.  The reference then
+ * moves to the candidate.  Reading of the paper: a skip that lands at or past
+ * the end of the item closes it; p_ref = 0 closes it too (no later pair can
+ * be an edge). */
 int64_t or_generate_item(const or_graph* g, const or_info* info, int64_t item, int64_t* v_out,
                          int64_t cap, or_stats* st) {
   int64_t u, j0, end;
@@ -264,28 +270,29 @@ int64_t or_generate_item(const or_graph* g, const or_info* info, int64_t item, i
   if (or_item_bounds(g, info, item, &u, &seg, &j0, &end) != 0) return -1;
   const double S = info->S;
   const uint32_t k0 = (uint32_t)g->seed, k1 = (uint32_t)(g->seed >> 32);
+  if (j0 >= end) return 0;
+  double Q_ref = Qof(g, info, u, j0); /* the item's first position sets the first bound */
+  int64_t pos = j0;                   /* first position the next skip can land on */
+  uint32_t draw = 0;                  /* index of the item's next Philox block */
   int64_t count = 0;
-  int64_t j = j0;
-  uint32_t t = 0;
-  if (j >= end) return 0;
-  double Qprev = Qof(g, info, u, j); /* p <- min(w_i w_j / S, 1) at the first position */
-  while (j < end && Qprev > 0.0) {
-    uint32_t b[4] = {t, seg, (uint32_t)u, (uint32_t)((uint64_t)u >> 32)};
+  for (;;) {
+    if (pos >= end || Q_ref <= 0.0) break;
+    uint32_t b[4] = {draw, seg, (uint32_t)u, (uint32_t)((uint64_t)u >> 32)};
     or_philox4x32_10(b, k0, k1);
-    ++t;
+    ++draw;
     if (st) st->iterations++;
-    int64_t R = end - j;
-    int64_t delta = 0;
-    if (Qprev != S) delta = or_skip(or_uniform53(b[0], b[1]), Qprev, S, R, st);
-    if (delta >= R) break; /* the candidate falls past the end of the item */
-    int64_t v = j + delta;
-    double Qv = Qof(g, info, u, v);
-    if (accept(g, b[2], b[3], Qprev, Qv)) {
-      if (count < cap && v_out) v_out[count] = v;
+    const int64_t room = end - pos;
+    /* p_ref = 1 (capped): every position is a candidate, no skip */
+    const int64_t skip = Q_ref == S ? 0 : or_skip(or_uniform53(b[0], b[1]), Q_ref, S, room, st);
+    if (skip >= room) break;
+    const int64_t cand = pos + skip;
+    const double Q_cand = Qof(g, info, u, cand);
+    if (accept(g, b[2], b[3], Q_ref, Q_cand)) {
+      if (count < cap && v_out) v_out[count] = cand;
       ++count;
     }
-    Qprev = Qv; /* p <- q */
-    j = v + 1;  /* j <- v + 1 */
+    Q_ref = Q_cand;
+    pos = cand + 1;
   }
   return count;
 }

@@ -272,10 +272,31 @@ def cl_calibrate(d_target, n: int, d_w, opts: cl_calib_opts | None, d_ws, ws_byt
     return st, {"iterations": rep.iterations, "max_rel_err": rep.max_rel_err, "S": rep.S}
 
 
+def _check_device_array(t, name: str, dtype, need: int):
+    """For torch tensors passed as device arrays: dtype, length and device
+    checked before the C call (a raw address is passed through unchecked)."""
+    if t is None or isinstance(t, int):
+        return
+    import torch
+
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must be a tensor on the current CUDA device")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() < need:
+        raise ValueError(f"{name} must be contiguous with at least {need} elements")
+
+
 def cl_scan_noalloc(d_counts, n: int, d_offsets, stream=None):
     """cl_scan without a plan, a workspace or any allocation (for callers that
     cannot allocate device memory); its scratch is a fixed array inside the
     library, so concurrent calls race.  n <= 2^28."""
+    import torch
+
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    _check_device_array(d_counts, "d_counts", torch.int32, n)
+    _check_device_array(d_offsets, "d_offsets", torch.int64, n + 1)
     _check(load_library().cl_scan_noalloc(_ptr(d_counts), n, _ptr(d_offsets), _stream(stream)), "cl_scan_noalloc")
 
 

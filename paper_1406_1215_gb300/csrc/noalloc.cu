@@ -12,12 +12,14 @@
 // the process exits (1 MiB + 8 bytes per device).
 //
 // Host code must not pass `g_noalloc_partials` itself to a kernel: on the
-// host that name is only a stand-in for the device symbol.  Its device
-// address is fetched once per device with cudaGetSymbolAddress while that
-// device is current, and that address is what the kernels receive.
+// host that name is only a stand-in for the device symbol.  Each call looks up
+// the array's device address with cudaGetSymbolAddress on the current device
+// and passes that address to the kernels.  The lookup is repeated on every
+// call rather than cached: after a cudaDeviceReset the library's device code
+// is loaded again and the array may sit at another address, so a cached
+// pointer could point into freed memory.  Once the device code is loaded the
+// lookup is cheap next to a kernel launch.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "cl_internal.cuh"
 
@@ -29,21 +31,12 @@ constexpr long long NOALLOC_MAX_TILES = NOALLOC_MAX_COUNTS / cl::SCAN_TILE_HOST;
 // The shared scratch: tile partials of the three-phase scan.
 static __device__ __align__(256) long long g_noalloc_partials[NOALLOC_MAX_TILES + 1];
 
-constexpr int MAX_DEVICES = 128;
-std::mutex g_mu;
-long long* g_dev_ptr[MAX_DEVICES] = {};
-
-// Device address of the scratch on the current device (set up on first use).
+// Device address of the scratch on the current device.  The first call on a
+// device also loads the library's device code there (lazy module loading).
 cl_status noalloc_scratch(long long** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return CL_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return CL_ERR_CUDA;
-    g_dev_ptr[dev] = (long long*)p;
-  }
-  *out = g_dev_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return CL_ERR_CUDA;
+  *out = (long long*)p;
   return CL_OK;
 }
 

@@ -45,8 +45,14 @@ def test_noalloc_scan_rejects_oversize_without_touching_output():
     P = lib()
     out = torch.full((4,), -1, dtype=torch.int64, device="cuda")
     counts = torch.zeros(3, dtype=torch.int32, device="cuda")
+    # raw addresses go straight to the C entry point, which refuses the size
     with pytest.raises(P.ClError) as ei:
-        P.cl_scan_noalloc(counts, (1 << 28) + 1, out)
+        P.cl_scan_noalloc(counts.data_ptr(), (1 << 28) + 1, out.data_ptr())
     assert ei.value.status == 4  # CL_ERR_RANGE
+    # tensors are checked by the binding before the call: too short, wrong dtype
+    with pytest.raises(ValueError):
+        P.cl_scan_noalloc(counts, 3, out[:3])
+    with pytest.raises(ValueError):
+        P.cl_scan_noalloc(counts.to(torch.int64), 3, out)
     torch.cuda.synchronize()
     assert bool((out == -1).all())
