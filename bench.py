@@ -48,11 +48,40 @@ KERNELS_PER_STEP = 18
 # ALU roofline of the dominant kernel (the staged count pass): one Philox4x32-10 block per
 # loop iteration is the irreducible arithmetic of the stream; a block needs 20 32x32->64-bit
 # multiplies; an SM issues 32 of them per clock (4 SMSPs x 32 lanes at the half-rate integer
-# multiply, two halves per wide product): 152 SMs x 32 / 20 x 2.07 GHz.
+# multiply, two halves per wide product): 152 SMs x 32 / 20 x 2.07 GHz.  The bench also
+# measures the rate itself (cl_diag_philox_rate) and reports the fraction of both.
 PHILOX_PEAK = 152 * 32 / 20 * 2.07e9
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one staged count launch on the
-# default workload, from a one-pass ncu capture of this kernel build; None once it has changed.
-STAGE_TRAFFIC_BYTES = 20996458496
+# DRAM traffic of the staged count launch comes from an ncu capture summarised in this file,
+# tied to the sampler's sources by their SHA-1: a changed kernel reports no traffic.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sample_kernel_stage_traffic_pl_n1e8.md")
+KERNEL_SOURCES = ["sample.cu", "clmath.cuh", "cl_internal.cuh", "philox.cuh", "ln_tables.h"]
+
+
+def kernel_sources_sha1() -> str:
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1406_1215_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def stage_traffic(workload: str):
+    """DRAM bytes per staged count launch of this kernel build on `workload`, or None."""
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_PROFILE):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_sources_sha1") != kernel_sources_sha1() or kv.get("workload") != workload:
+        return None
+    try:
+        return int(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def peaks():
@@ -284,6 +313,8 @@ def run_ours(args, rank: int, world: int):
     step_each = [a.elapsed_time(b) for a, b in kern["step"]]
     m_step = ms[-1]
     peak, how = peaks()
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    philox_rate = P.cl_diag_philox_rate(1 << 12, 42, sink, sh)  # measured Philox blocks/s
     step_s = elapsed / args.steps
     alu = iterations / t_count
 
@@ -296,15 +327,17 @@ def run_ours(args, rank: int, world: int):
         graph2 = P.cl_graph(n, P.CL_W_I32, w_dev.data_ptr(), seed, 8192.0)
         e_steps = max(1, min(args.steps, 5))
 
+        # the plan is created once (validation, exact S, item space: host-side analysis of these
+        # weights, which do not change between steps); every step uploads the weights again,
+        # rebuilds the device-side plan from them (prefixes, Eq. 1 costs, Eq. 3 tasks) and runs
+        # count + scan + emit by item ranges with each range's host copy (copy engines)
+        # overlapping the sampling of the next
+        pl = P.cl_plan_create([graph2], tun, scratch, sb, sh)
+
         def e2e_step():
             w_dev.copy_(w_host, non_blocking=True)
-            pl = P.cl_plan_create([graph2], tun, scratch, sb, sh)
             P.cl_plan_build(pl, ws, wb, sh)
-            # count + scan + emit by item ranges; each range's host copy (copy engines)
-            # overlaps the sampling of the next
-            mm = P.cl_generate_host(pl, P.CL_E_I32, out_host, cap, edges, counts, offsets, 0, 0, sh)
-            P.cl_plan_destroy(pl)
-            return mm
+            return P.cl_generate_host(pl, P.CL_E_I32, out_host, cap, edges, counts, offsets, 0, 0, sh)
 
         def link_gbps():
             # device -> pinned host rate of a plain 4 GB copy: the floor of this leg, which
@@ -317,9 +350,9 @@ def run_ours(args, rank: int, world: int):
             torch.cuda.synchronize()
             return 8 * k / (x.elapsed_time(y) / 1e3) / 1e9
 
-        e2e_step()
+        e2e_step()  # warm-up: the plan's host pipeline (streams, events) is made on first use
         torch.cuda.synchronize()
-        link0 = link_gbps()
+        links = [link_gbps()]
         marks = [ev() for _ in range(e_steps + 1)]
         marks[0].record(stream)
         em = []
@@ -328,11 +361,15 @@ def run_ours(args, rank: int, world: int):
             marks[i + 1].record(stream)
         torch.cuda.synchronize()
         et = marks[0].elapsed_time(marks[-1]) / 1e3
-        link1 = link_gbps()
+        links.append(link_gbps())
+        P.cl_plan_destroy(pl)
+        step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(e_steps)]
         e2e = {"value": sum(em) / et, "unit": "edges/s", "h2d_bytes_per_step": 4 * n,
                "d2h_bytes_per_step": 8 * em[-1], "steps": e_steps,
-               "step_ms": [marks[i].elapsed_time(marks[i + 1]) for i in range(e_steps)],
-               "link_d2h_gbps": [link0, link1]}
+               "step_ms": step_ms, "step_ms_median": statistics.median(step_ms), "step_ms_min": min(step_ms),
+               "link_d2h_gbps": links,
+               "link_bound_ms": 8 * em[-1] / (max(links) * 1e9) * 1e3,
+               "plan": "created once; weights uploaded and device-side plan rebuilt every step"}
         del out_host, w_host
 
     # free the main leg's buffers (tens of GB) before the other legs
@@ -352,9 +389,11 @@ def run_ours(args, rank: int, world: int):
         "edges_per_step": m_step,
         "roofline": {"bound": "alu", "achieved": alu, "peak": PHILOX_PEAK, "unit": "Philox blocks/s",
                      "frac": alu / PHILOX_PEAK,
-                     "traffic": STAGE_TRAFFIC_BYTES if args.workload == "pl_n1e8" else None,
+                     "traffic": stage_traffic(args.workload),
                      "kernel": "sample_kernel<STAGE> (staged count pass)", "iterations_per_launch": iterations,
-                     "peak_source": "derived from SM count, integer-multiply issue rate and max clock"},
+                     "peak_source": "derived from SM count, integer-multiply issue rate and max clock",
+                     "peak_measured": philox_rate, "frac_of_measured": alu / philox_rate,
+                     "peak_measured_source": "cl_diag_philox_rate: Philox4x32-10 blocks/s on this GPU, this run"},
         "hbm_write_roofline": {"achieved": 8.0 * m_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
                                "frac": 8.0 * m_step / step_s / 1e9 / peak, "peak_source": how,
                                "algorithmic_bytes": "8 B per edge (int32 pair) per step"},
@@ -388,8 +427,9 @@ def batch_leg(P, dev, args):
     views = [W[int(offs[i]):int(offs[i + 1])] for i in range(len(work))]
     seeds = [s for _, s in work]
     G = len(views)
-    knobs, timings = autotune.tune(views, seeds, reps=1, use_cache=False,
-                                   candidates=[{}, {"block": 128}, {"blocks_per_sm": 2}, {"tasks": 1 << 18}])
+    # ten candidates (task granularity, block size, blocks per SM), each checked to reproduce the
+    # first candidate's output element for element
+    knobs, timings = autotune.tune(views, seeds, reps=1, use_cache=False)
     gen = Generator(views, seeds, **knobs)
     gen.count()
     m = gen.scan(True)

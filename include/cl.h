@@ -99,11 +99,13 @@ typedef struct {
                           * items take the regeneration path (for testing that path) */
   int32_t partition;     /* task split: CL_PART_UCP (0, default) = equal Eq. 1 cost per task
                           * (Eq. 3, the uniform cost partition); CL_PART_CP (1) = equal node counts
-                          * (the paper's consecutive partition, Section 4), for comparing the two;
-                          * other values: CL_ERR_INVALID_ARG */
+                          * (the paper's consecutive partition, Section 4); CL_PART_RRP (2) = round
+                          * robin (Section 4): task t holds the items t, t + T, t + 2T, ...; the
+                          * last two are for comparing partitions (cl_generate_host refuses
+                          * CL_PART_RRP); other values: CL_ERR_INVALID_ARG */
 } cl_tuning;
 
-enum { CL_PART_UCP = 0, CL_PART_CP = 1 };
+enum { CL_PART_UCP = 0, CL_PART_CP = 1, CL_PART_RRP = 2 };
 
 typedef struct {
   int64_t n, H;           /* nodes, heavy rows */
@@ -160,18 +162,50 @@ cl_status cl_plan_workspace_bytes(const cl_plan* plan, size_t* bytes);
 cl_status cl_plan_build(cl_plan* plan, void* d_ws, size_t ws_bytes, cl_stream_t stream);
 
 cl_status cl_plan_items(const cl_plan* plan, int64_t* n_items);
+
+/* The task split that cl_plan_build made (Section 4: Eq. 1-2 costs, Eq. 3
+ * boundaries), for inspection and tests.  *T = number of tasks (always set).
+ * d_task_start (nullable, T + 1 int64): task t holds the items
+ * [d_task_start[t], d_task_start[t + 1]) (Eq. 3's lower boundaries n_t, with
+ * d_task_start[T] = n_items); under CL_PART_RRP task t holds the items
+ * t, t + T, t + 2T, ... and d_task_start[t] = min(t, n_items).
+ * d_cost_prefix (nullable, n_items int64): the inclusive prefix C_i of the
+ * item costs c_i = c0 + (w_u / S) sum_{v in item} w_v in units of 1/16 edge
+ * (c0 = 4 edges; each term rounded to the unit from single precision).
+ * Asynchronous device-to-device copies on `stream`; requires cl_plan_build. */
+cl_status cl_plan_tasks(const cl_plan* plan, int32_t* T, int64_t* d_task_start, int64_t* d_cost_prefix,
+                        cl_stream_t stream);
 cl_status cl_plan_graph_info(const cl_plan* plan, int32_t g, cl_graph_info* out);
+
+/* Per-task timing of the count passes (the runtime-follows-cost measurement of
+ * Section 5, Figs. 1 and 5, at task granularity).  d_task_ns: a caller-owned
+ * device array of 2 T uint64 (T from cl_plan_tasks), or NULL to stop.  Every
+ * later count pass stores, for each task a warp takes, the GPU's global timer
+ * (ns) at the moment the warp took it (d_task_ns[2t]) and at the moment the
+ * same warp took its next task or finished (d_task_ns[2t + 1]) -- with one task
+ * per warp, the task's run time.  Entries of tasks no warp took are left as
+ * they were.  Host-side setting only; no synchronisation. */
+cl_status cl_plan_task_clock(cl_plan* plan, uint64_t* d_task_ns);
+
+/* The launch shape of the count pass: grid (blocks; persistent, resident
+ * blocks per SM times SMs) and threads per block.  T = count_grid * block / 32
+ * tasks give one task per resident warp. */
+cl_status cl_plan_launch_info(const cl_plan* plan, int32_t* count_grid, int32_t* block);
 
 /* --- sampling (Algorithm 1, Create-Edges, per item) ---------------------- */
 
-/* Count pass: d_counts[i] = number of edges of global item i (int32, n_items
+/* Count pass (Algorithm 1, Create-Edges, run per item with the stream above;
+ * Section 3): d_counts[i] = number of edges of global item i (int32, n_items
  * entries, caller-owned).  Unless the tuning disabled staging, the pass also
  * stores each item's destination nodes, in order, in the plan workspace, so
  * that cl_emit only has to copy them (the sampling arithmetic runs once).
  * Asynchronous. */
 cl_status cl_count(cl_plan* plan, int32_t* d_counts, cl_stream_t stream);
 
-/* Exclusive scan of the counts: d_offsets[i] = sum_{k<i} d_counts[k] for
+/* Exclusive scan of the counts -- the prefix-sum step of Calc-Cost
+ * (Algorithm 2, Section 4) applied to the items' edge counts instead of their
+ * costs, which places every item's edges in one array in canonical order:
+ * d_offsets[i] = sum_{k<i} d_counts[k] for
  * i = 0..n_items (n_items + 1 int64 entries; d_offsets[n_items] = m).  If
  * h_total is non-null the call SYNCHRONIZES and writes m there, and reports a
  * pending device error as CL_ERR_DEVICE.  d_counts and d_offsets must not
@@ -179,7 +213,8 @@ cl_status cl_count(cl_plan* plan, int32_t* d_counts, cl_stream_t stream);
 cl_status cl_scan(cl_plan* plan, const int32_t* d_counts, int64_t* d_offsets, int64_t* h_total,
                   cl_stream_t stream);
 
-/* Emit pass: writes the edges of items [item_begin, item_end) -- copied from
+/* Emit pass (Algorithm 1's output: the accepted pairs (u, v); Section 3): writes the
+ * edges of items [item_begin, item_end) -- copied from
  * the staging of the last cl_count when there is one, otherwise (and for items
  * that did not fit in the staging pool) regenerated -- edge k of
  * item i to d_edges[d_offsets[i] - d_offsets[item_begin] + k] as a (u, v)
@@ -191,7 +226,8 @@ cl_status cl_scan(cl_plan* plan, const int32_t* d_counts, int64_t* d_offsets, in
 cl_status cl_emit(cl_plan* plan, const int64_t* d_offsets, int32_t etype, void* d_edges, int64_t capacity,
                   int64_t item_begin, int64_t item_end, cl_stream_t stream);
 
-/* cl_count + cl_scan + cl_emit over all items in one call, with no host
+/* Algorithm 1 over every item (Section 3) with the count prefix of Algorithm 2
+ * placing the edges: cl_count + cl_scan + cl_emit over all items in one call, with no host
  * round trip: d_counts and d_offsets are filled as by cl_count and cl_scan,
  * edge k of item i goes to d_edges[d_offsets[i] + k].  h_total (nullable):
  * synchronizes and returns m; m > capacity returns CL_ERR_CAPACITY (nothing is
@@ -199,7 +235,9 @@ cl_status cl_emit(cl_plan* plan, const int64_t* d_offsets, int32_t etype, void* 
 cl_status cl_generate(cl_plan* plan, int32_t etype, void* d_edges, int64_t capacity, int32_t* d_counts,
                       int64_t* d_offsets, int64_t* h_total, cl_stream_t stream);
 
-/* Count + scan + emit for every graph of the plan, with no host round trip:
+/* Algorithm 1 (Section 3) for every graph of a multi-graph plan, the items of
+ * all graphs in one item space split by Eq. 3 (Section 4):
+ * count + scan + emit for every graph of the plan, with no host round trip:
  * graph g's edges start at d_graph_offsets[g] (G + 1 int64 entries,
  * d_graph_offsets[G] = total edges) and carry the graph's local vertex ids.
  * d_counts (n_items int32) and d_offsets (n_items + 1 int64) are caller
@@ -276,7 +314,9 @@ size_t cl_calibrate_workspace_bytes(int64_t n);
 cl_status cl_calibrate(const double* d_target, int64_t n, double* d_w, const cl_calib_opts* opts,
                        cl_calib_report* report, void* d_ws, size_t ws_bytes, cl_stream_t stream);
 
-/* SYNCHRONIZING: the run statistics of the last cl_count (flagged skips) and
+/* Work counters of Algorithm 1's loop (Section 3; Eq. 1 models an item's work
+ * as its edges + 1, the realized work is its loop iterations):
+ * SYNCHRONIZING: the run statistics of the last cl_count (flagged skips) and
  * the device error word; resets the counters. */
 cl_status cl_stats(cl_plan* plan, cl_run_stats* out, cl_stream_t stream);
 
@@ -325,6 +365,15 @@ cl_status cl_diag_neglog(const uint64_t* d_A, const uint64_t* d_B, int64_t count
  * d_tier[i] = 0 (float-float decided), 1 (double-double decided), 2 (tie: nearest integer). */
 cl_status cl_diag_skip(const uint64_t* d_a, const uint64_t* d_Q, const uint64_t* d_S, const int64_t* d_R,
                        int64_t count, int64_t* d_delta, int32_t* d_tier, cl_stream_t stream);
+
+/* Throughput of the sampler's random stream on this GPU: Philox4x32-10 blocks
+ * per second (into *blocks_per_s) over a grid of resident blocks, each thread
+ * running `iters` dependent blocks.  One block is drawn per loop iteration of
+ * Algorithm 1, so the rate is an upper bound on the sampler's iterations per
+ * second (the measured peak of its arithmetic roofline).  d_sink: one
+ * caller-owned device uint64 (written only by a chance match).  SYNCHRONIZING. */
+cl_status cl_diag_philox_rate(int64_t iters, uint64_t seed, uint64_t* d_sink, double* blocks_per_s,
+                              cl_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -108,7 +108,8 @@ def lib():
         L.or_expected_edges_bruteforce_i32.argtypes = [vp, i64, _P(u64), _P(u64)]
         for name in ("or_expected_degree", "or_expected_degree_bruteforce"):
             getattr(L, name).argtypes = [vp, i64, dbl, vp]
-        for name in ("or_expected_degree_adjoint", "or_expected_degree_adjoint_bruteforce"):
+        for name in ("or_expected_degree_adjoint", "or_expected_degree_adjoint_bruteforce",
+                     "or_expected_degree_adjoint_pairwise"):
             getattr(L, name).argtypes = [vp, i64, dbl, vp, vp]
         _lib = L
     return _lib
@@ -279,11 +280,18 @@ def expected_degree(w: np.ndarray, S: float | None = None, brute: bool = False) 
 
 
 def expected_degree_adjoint(w: np.ndarray, gE: np.ndarray, S: float | None = None,
-                            brute: bool = False) -> np.ndarray:
+                            brute: bool = False, pairwise: bool = False) -> np.ndarray:
+    """Gradient of sum_u gE_u E_u(w).  brute: O(n^3) term by term; pairwise: O(n^2)
+    pair sums; default: O(n log n) with sorted cap thresholds and suffix sums."""
     w = np.ascontiguousarray(w, dtype=np.float64)
     gE = np.ascontiguousarray(gE, dtype=np.float64)
     S = weight_sum_f64(w) if S is None else S
     g = np.empty(max(len(w), 1), dtype=np.float64)
-    fn = lib().or_expected_degree_adjoint_bruteforce if brute else lib().or_expected_degree_adjoint
+    if brute:
+        fn = lib().or_expected_degree_adjoint_bruteforce
+    elif pairwise:
+        fn = lib().or_expected_degree_adjoint_pairwise
+    else:
+        fn = lib().or_expected_degree_adjoint
     fn(_ptr(w), len(w), S, _ptr(gE), _ptr(g))
     return g[: len(w)]

@@ -542,3 +542,29 @@ void or_expected_degree_adjoint_bruteforce(const double* w, int64_t n, double S,
     gw[k] = (double)acc;
   }
 }
+
+/* The same gradient in O(n^2), every sum taken pair by pair from the pairwise
+ * definition (no sorted thresholds, no suffix sums), for n in the thousands.
+ * With f_uv = w_u w_v / S on an uncapped pair (fl(w_u w_v) < S) and a
+ * constant 1 on a capped one (derivative 0), S = sum_k w_k:
+ *   d f_uv / d w_k = ([u = k] w_v + [v = k] w_u) / S - w_u w_v / S^2,
+ * and summing gE_u d f_uv / d w_k over ordered pairs u != v:
+ *   dL/dw_k = (gE_k A_k + B_k - K) / S,
+ *   A_u = sum_{v != u, (u,v) uncapped} w_v,
+ *   B_k = sum_{u != k, (u,k) uncapped} gE_u w_u,
+ *   K = sum_u gE_u w_u A_u / S. */
+void or_expected_degree_adjoint_pairwise(const double* w, int64_t n, double S, const double* gE, double* gw) {
+  long double* A = (long double*)calloc((size_t)(n > 0 ? n : 1), sizeof(long double));
+  long double* B = (long double*)calloc((size_t)(n > 0 ? n : 1), sizeof(long double));
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t v = 0; v < n; ++v) {
+      if (v == u || w[u] * w[v] >= S) continue;
+      A[u] += (long double)w[v];
+      B[u] += (long double)gE[v] * (long double)w[v];
+    }
+  long double K = 0;
+  for (int64_t u = 0; u < n; ++u) K += (long double)gE[u] * (long double)w[u] * A[u] / (long double)S;
+  for (int64_t k = 0; k < n; ++k) gw[k] = (double)(((long double)gE[k] * A[k] + B[k] - K) / (long double)S);
+  free(A);
+  free(B);
+}

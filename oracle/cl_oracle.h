@@ -107,6 +107,8 @@ void or_expected_degree_bruteforce(const double* w, int64_t n, double S, double*
 void or_expected_degree_adjoint(const double* w, int64_t n, double S, const double* gE, double* gw);
 void or_expected_degree_adjoint_bruteforce(const double* w, int64_t n, double S,
                                            const double* gE, double* gw);
+/* The same gradient in O(n^2), summed pair by pair (no thresholds or suffix sums). */
+void or_expected_degree_adjoint_pairwise(const double* w, int64_t n, double S, const double* gE, double* gw);
 
 #ifdef __cplusplus
 }

@@ -25,7 +25,7 @@ STATUS_NAMES = {
  CL_ERR_TIMEOUT, CL_ERR_CUDA, CL_ERR_STATE, CL_ERR_DEVICE) = range(1, 11)
 CL_W_I32, CL_W_F64 = 0, 1
 CL_E_I32, CL_E_I64 = 0, 1
-CL_PART_UCP, CL_PART_CP = 0, 1
+CL_PART_UCP, CL_PART_CP, CL_PART_RRP = 0, 1, 2
 HEAVY_W_DEFAULT = 8192.0
 
 
@@ -86,6 +86,9 @@ def load_library(path: str | None = None):
         "cl_plan_build": ([vp, vp, sz, vp], i32),
         "cl_plan_items": ([vp, P(i64)], i32),
         "cl_plan_graph_info": ([vp, i32, P(cl_graph_info)], i32),
+        "cl_plan_tasks": ([vp, P(i32), vp, vp, vp], i32),
+        "cl_plan_task_clock": ([vp, vp], i32),
+        "cl_plan_launch_info": ([vp, P(i32), P(i32)], i32),
         "cl_count": ([vp, vp, vp], i32),
         "cl_scan": ([vp, vp, vp, P(i64), vp], i32),
         "cl_emit": ([vp, vp, i32, vp, i64, i64, i64, vp], i32),
@@ -99,6 +102,7 @@ def load_library(path: str | None = None):
         "cl_diag_philox_curand": ([vp, i64, u64, vp, vp], i32),
         "cl_diag_neglog": ([vp, vp, i64, vp, vp, vp], i32),
         "cl_diag_skip": ([vp, vp, vp, vp, i64, vp, vp, vp], i32),
+        "cl_diag_philox_rate": ([i64, u64, vp, P(ctypes.c_double), vp], i32),
         "cl_scan_noalloc": ([vp, i64, vp, vp], i32),
         "cl_expected_degree_workspace_bytes": ([i64], sz),
         "cl_expected_degree": ([vp, i64, ctypes.c_double, vp, vp, sz, vp], i32),
@@ -175,6 +179,29 @@ def cl_plan_items(plan) -> int:
     n = ctypes.c_int64()
     _check(load_library().cl_plan_items(plan, ctypes.byref(n)), "cl_plan_items")
     return n.value
+
+
+def cl_plan_tasks(plan, d_task_start=None, d_cost_prefix=None, stream=None) -> int:
+    """Number of tasks T; copies the task table (T + 1 int64) and the item cost
+    prefix (n_items int64, 1/16-edge units) into the given device arrays."""
+    T = ctypes.c_int32()
+    st = load_library().cl_plan_tasks(plan, ctypes.byref(T), _ptr(d_task_start), _ptr(d_cost_prefix),
+                                      _stream(stream))
+    _check(st, "cl_plan_tasks")
+    return T.value
+
+
+def cl_plan_task_clock(plan, d_task_ns):
+    """Count passes record per-task global-timer stamps into d_task_ns (2 T uint64 /
+    int64 device array), or stop doing so when it is None."""
+    _check(load_library().cl_plan_task_clock(plan, _ptr(d_task_ns)), "cl_plan_task_clock")
+
+
+def cl_plan_launch_info(plan):
+    """(count-pass grid, threads per block)."""
+    g, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().cl_plan_launch_info(plan, ctypes.byref(g), ctypes.byref(b)), "cl_plan_launch_info")
+    return g.value, b.value
 
 
 def cl_plan_graph_info(plan, g: int) -> cl_graph_info:
@@ -318,6 +345,14 @@ def cl_diag_skip(d_a, d_Q, d_S, d_R, count: int, d_delta, d_tier, stream=None):
     st = load_library().cl_diag_skip(_ptr(d_a), _ptr(d_Q), _ptr(d_S), _ptr(d_R), count, _ptr(d_delta), _ptr(d_tier),
                                      _stream(stream))
     _check(st, "cl_diag_skip")
+
+
+def cl_diag_philox_rate(iters: int, seed: int, d_sink, stream=None) -> float:
+    """Philox4x32-10 blocks per second on this GPU (synchronizing)."""
+    r = ctypes.c_double()
+    _check(load_library().cl_diag_philox_rate(iters, seed, _ptr(d_sink), ctypes.byref(r), _stream(stream)),
+           "cl_diag_philox_rate")
+    return r.value
 
 
 from .generator import Generator, generate  # noqa: E402  (convenience layer over the C ABI)

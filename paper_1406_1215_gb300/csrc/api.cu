@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "cl_internal.cuh"
+#include "philox.cuh"
 
 using namespace cl;
 
@@ -56,6 +57,7 @@ struct cl_plan {
   unsigned* d_ovf_count = nullptr;
   unsigned long long* d_blk = nullptr;
   unsigned* d_snap = nullptr;  // per-chunk snapshots of the regeneration list length
+  unsigned long long* d_task_ns = nullptr;  // caller's per-task clock array (nullable)
   // host-output pipeline (cl_generate_host): a second stream and its events, made on first use
   cudaStream_t side = nullptr;
   cudaStream_t aux = nullptr;  // counts the second range beside the first
@@ -184,6 +186,8 @@ DevPlan dev_plan(const cl_plan* p) {
   P.wf64 = p->wtype == CL_W_F64 ? 1 : 0;
   P.pool_cap = p->pool_cap;
   P.blk = p->d_blk;
+  P.rrp = p->partition == CL_PART_RRP ? 1 : 0;
+  P.task_ns = p->d_task_ns;
   return P;
 }
 
@@ -253,6 +257,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     d.wtype = wtype;
     d.key0 = (unsigned)graphs[g].seed;
     d.key1 = (unsigned)(graphs[g].seed >> 32);
+    round_keys(d.key0, d.key1, d.rk);
     blk[g + 1] = blk[g] + (graphs[g].n + ANALYZE_CHUNK_HOST - 1) / ANALYZE_CHUNK_HOST;
     hw[g] = graphs[g].heavy_w;
   }
@@ -359,7 +364,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
   p->stage = !(tuning && tuning->no_stage);
   p->tiny_slots = tuning && tuning->stage_factor < 0;
   p->partition = tuning ? tuning->partition : CL_PART_UCP;
-  if (p->partition != CL_PART_UCP && p->partition != CL_PART_CP) {
+  if (p->partition != CL_PART_UCP && p->partition != CL_PART_CP && p->partition != CL_PART_RRP) {
     delete p;
     return CL_ERR_INVALID_ARG;
   }
@@ -454,6 +459,38 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
 cl_status cl_plan_items(const cl_plan* plan, int64_t* n_items) {
   if (!plan || !n_items) return CL_ERR_INVALID_ARG;
   *n_items = plan->n_items;
+  return CL_OK;
+}
+
+cl_status cl_plan_tasks(const cl_plan* p, int32_t* T, int64_t* d_task_start, int64_t* d_cost_prefix,
+                        cl_stream_t stream) {
+  if (!p || !T) return CL_ERR_INVALID_ARG;
+  *T = p->T;
+  if (!d_task_start && !d_cost_prefix) return CL_OK;
+  if (!p->built) return CL_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cl_status st;
+  if (d_task_start &&
+      (st = cuda_ok(cudaMemcpyAsync(d_task_start, p->d_task, sizeof(int64_t) * (p->T + 1), cudaMemcpyDeviceToDevice,
+                                    s))))
+    return st;
+  if (d_cost_prefix && p->n_items > 0 &&
+      (st = cuda_ok(cudaMemcpyAsync(d_cost_prefix, p->d_C, sizeof(int64_t) * p->n_items, cudaMemcpyDeviceToDevice,
+                                    s))))
+    return st;
+  return CL_OK;
+}
+
+cl_status cl_plan_task_clock(cl_plan* p, uint64_t* d_task_ns) {
+  if (!p) return CL_ERR_INVALID_ARG;
+  p->d_task_ns = (unsigned long long*)d_task_ns;
+  return CL_OK;
+}
+
+cl_status cl_plan_launch_info(const cl_plan* p, int32_t* count_grid, int32_t* block) {
+  if (!p || !count_grid || !block) return CL_ERR_INVALID_ARG;
+  *count_grid = p->grid_count;
+  *block = p->block;
   return CL_OK;
 }
 
@@ -586,6 +623,7 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   if (p->n_items > 0 && !d_counts) return CL_ERR_INVALID_ARG;
   if (capacity > 0 && !h_edges) return CL_ERR_INVALID_ARG;
   if (chunks < 0 || chunks > CL_HOST_MAX_CHUNKS || copy_sms < 0) return CL_ERR_INVALID_ARG;
+  if (p->partition == CL_PART_RRP) return CL_ERR_INVALID_ARG;  // ranges of consecutive items need Eq. 3 or CP tasks
   if (!p->built) return CL_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   cl_status st;

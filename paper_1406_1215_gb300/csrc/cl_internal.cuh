@@ -53,6 +53,7 @@ struct DevGraph {
   long long S_i;          // exact integer sum (integer weights)
   double S_d;             // weight sum as a double
   unsigned key0, key1;    // Philox key = seed
+  unsigned rk[20];        // Philox round keys of that key (key + r * Weyl constants)
   long long H;            // heavy rows (w_u >= heavy_w): a prefix
   long long Hh;           // heavy rows that have items: min(H, n - 1)
   long long n_heavy;      // items of the heavy rows
@@ -237,6 +238,9 @@ struct DevPlan {
   unsigned ovf_cap;
   int wf64;                     // the plan's weights are doubles
   const unsigned long long* blk;  // integer weights: uniform-block table (BLK_MIXED or (w << 32) | run end)
+  int rrp;                      // round-robin partition: task t holds the items t, t + T, t + 2T, ...
+  unsigned long long* task_ns;  // nullable: per task, the global timer (ns) when a warp took it and
+                                // when that warp took its next task or finished (count passes)
 };
 
 // Staging slot of item i in entries (0: the item is never staged, its slot

@@ -78,9 +78,56 @@ __global__ void diag_skip_kernel(const unsigned long long* __restrict__ a, const
   tier[i] = tr;
 }
 
+// Philox4x32-10 throughput: every thread runs `iters` blocks, each keyed by
+// the previous block's output (no work can be hoisted or skipped), and folds
+// them into one word.  The rate bounds the sampler from above: one block per
+// loop iteration of Algorithm 1.
+__global__ void __launch_bounds__(256) diag_philox_rate_kernel(long long iters, uint32_t k0, uint32_t k1,
+                                                                unsigned long long* __restrict__ sink) {
+  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+  u32x4 c{tid, 0u, tid * 2654435761u, 0u};
+  uint32_t acc = 0;
+  for (long long i = 0; i < iters; ++i) {
+    const u32x4 r = philox4x32_10(c, k0, k1);
+    acc ^= r.x ^ r.y ^ r.z ^ r.w;
+    c = u32x4{(uint32_t)i + 1u, r.y, c.z, r.w};
+  }
+  if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);  // keeps the chain live
+}
+
 }  // namespace cl
 
 using namespace cl;
+
+extern "C" cl_status cl_diag_philox_rate(int64_t iters, uint64_t seed, uint64_t* d_sink, double* blocks_per_s,
+                                         cl_stream_t stream) {
+  if (iters <= 0 || !d_sink || !blocks_per_s) return CL_ERR_INVALID_ARG;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CL_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, diag_philox_rate_kernel, 256, 0);
+  const int grid = sms * (per_sm > 0 ? per_sm : 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return CL_ERR_CUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return CL_ERR_CUDA;
+  }
+  diag_philox_rate_kernel<<<grid, 256, 0, s>>>(iters / 8 > 0 ? iters / 8 : 1, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                               (unsigned long long*)d_sink);  // warm-up
+  cudaEventRecord(a, s);
+  diag_philox_rate_kernel<<<grid, 256, 0, s>>>(iters, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                               (unsigned long long*)d_sink);
+  cudaEventRecord(b, s);
+  cl_status st = cudaEventSynchronize(b) == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+  float ms = 0;
+  if (st == CL_OK && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) st = CL_ERR_CUDA;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st == CL_OK) *blocks_per_s = (double)grid * 256.0 * (double)iters / (ms * 1e-3);
+  return st;
+}
 
 static cl_status diag_done() { return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA; }
 

@@ -30,6 +30,26 @@ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The same with the round keys precomputed: rk[2r], rk[2r+1] = key + r * Weyl
+// constants (round_keys below), so that a kernel parameter holds them.
+__device__ __forceinline__ u32x4 philox4x32_10_rk(u32x4 c, const uint32_t (&rk)[20]) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = u32x4{hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0};
+  }
+  return c;
+}
+
+__host__ __device__ inline void round_keys(uint32_t k0, uint32_t k1, uint32_t (&rk)[20]) {
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+}
+
 // The 52 random bits of a word pair: r = (2k+1) / 2^53 in (0, 1).
 __device__ __forceinline__ unsigned long long grid52(uint32_t lo, uint32_t hi) {
   return (((unsigned long long)hi << 32) | lo) >> 12;

@@ -557,6 +557,14 @@ __global__ void cp_bounds_kernel(const DevGraph* __restrict__ gs, int G, long lo
   task_start[t] = g.item_begin + first;
 }
 
+// Round robin (RRP, Section 4): task t holds the items t, t + T, t + 2T, ...;
+// its table entry is its first item.
+__global__ void rrp_bounds_kernel(long long n_items, long long* __restrict__ task_start, int T) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t > T) return;
+  task_start[t] = t == T ? n_items : (t < n_items ? t : n_items);
+}
+
 long long scan_partials_needed(long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, bool f64, const void* d_P,
@@ -578,7 +586,9 @@ void launch_costs_and_tasks(const DevGraph* d_graphs, int G, long long n_items, 
   tile_reduce_i64_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
   partials_scan_kernel<long long><<<1, 1024, 0, s>>>(d_partials, nt, nullptr);
   tile_incl_scan_i64_kernel<<<(unsigned)nt, PLAN_THREADS, 0, s>>>(d_C, n_items, d_partials);
-  if (partition == CL_PART_CP)
+  if (partition == CL_PART_RRP)
+    rrp_bounds_kernel<<<(T + 1 + 255) / 256, 256, 0, s>>>(n_items, d_task_start, T);
+  else if (partition == CL_PART_CP)
     cp_bounds_kernel<<<(T + 1 + 255) / 256, 256, 0, s>>>(d_graphs, G, n_nodes, n_items, d_task_start, T);
   else
     task_bounds_kernel<<<(T + 1 + 255) / 256, 256, 0, s>>>(d_C, n_items, d_task_start, T);

@@ -37,11 +37,20 @@
 namespace cl {
 
 constexpr int SAMPLER_THREADS = 256;
+// resident blocks per SM the sampler is compiled for: 3 x 256 threads leave 85 registers
+// per thread, enough for the loop state without spills (4 blocks: 64 registers, spills)
+constexpr int SAMPLER_MIN_BLOCKS = 3;
 constexpr unsigned GROUP = 8;  // entries per staged write: one 32-byte sector
 
 enum { MODE_COUNT = 0, MODE_STAGE = 1, MODE_EMIT = 2 };
 
 __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Exact test (2k+1) * Qprev < 2^53 * Qv for 0 <= Qv < Qprev < 2^53.
 __device__ __forceinline__ bool accept_i(unsigned long long k, unsigned long long Qprev, unsigned long long Qv) {
@@ -106,8 +115,62 @@ struct Wt<true> {
   }
 };
 
+// Philox keys of a lane's item: the precomputed round keys of a single-graph
+// plan (kernel parameter, so the key schedule costs no instruction), or the
+// seed of the lane's graph in a batch.
+template <bool SINGLE>
+struct Keys;
+template <>
+struct Keys<true> {
+  __device__ __forceinline__ u32x4 draw(const DevGraph& g, unsigned t, unsigned seg, unsigned u) const {
+    return philox4x32_10_rk(u32x4{t, seg, u, 0u}, g.rk);
+  }
+};
+template <>
+struct Keys<false> {
+  unsigned k0, k1;
+  __device__ __forceinline__ u32x4 draw(const DevGraph&, unsigned t, unsigned seg, unsigned u) const {
+    return philox4x32_10(u32x4{t, seg, u, 0u}, k0, k1);
+  }
+};
+
+// Acceptance r_a < Q_t / Q_prev with Q_t <= Q_prev, exactly.  Integer weights:
+// while Q_prev < S neither product is capped and the ratio is w_t / w_prev
+// (w_u cancels): (2k+1) w_prev < 2^53 w_t, with 2k+1 < 2^53 and w < 2^31, is
+// L < w_t 2^21 for L = floor((2k+1) w_prev / 2^32) (the low 32 bits of the
+// product cannot decide it); a capped Q_prev = S takes the 128-bit test.
+__device__ __forceinline__ bool accept_ratio(unsigned long long k, unsigned w_prev, unsigned w_t) {
+  const unsigned long long a = 2ull * k + 1ull;
+  const unsigned a_lo = (unsigned)a, a_hi = (unsigned)(a >> 32);
+  const unsigned long long L = (unsigned long long)a_hi * w_prev + __umulhi(a_lo, w_prev);
+  return L < ((unsigned long long)w_t << 21);
+}
+
+// A warp's queue of up to 32 upcoming items with their set-up data, and the
+// feed it is filled from (shared memory; see sample_kernel).
+template <typename w_t>
+struct WarpQueue {
+  long long item[32];
+  unsigned long long sb[32];  // STAGE: slot base; EMIT: output position of the item's first edge
+  long long cnt[32];          // EMIT: the item's edge count
+  unsigned u[32], seg[32], ss[32];
+  int g[32];
+  w_t w[32];
+  unsigned ok;                // bit r: entry r holds an item to run
+  int tasks_left, cg;
+  unsigned rtask, cu, cseg;   // round robin: the task's first item; consecutive: cursor at fnext
+  long long fnext, fend;      // items (or list entries, or round-robin steps) not yet queued
+};
+
+// The persistent sampling kernel.  Lanes run items; a warp keeps a queue of
+// up to 32 upcoming items of its current task, one per lane, with their
+// set-up data (row, segment, w_u, staging slot or output offset) loaded
+// ahead, 32 items at a time with coalesced loads; a lane whose item ends takes
+// the next queue entry by shuffle.  Queue sources: consecutive items of an
+// Eq. 3 task (a warp cursor walks row/segment positions), the regeneration
+// list (EMIT), or the strided items of a round-robin task.
 template <int MODE, bool SINGLE, bool WF, typename E>
-__global__ void __launch_bounds__(SAMPLER_THREADS, 4)
+__global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
     sample_kernel(DevPlan P, DevGraph G1, long long ib, long long ie, const long long* __restrict__ offsets,
                   E* __restrict__ edges, long long capacity, int* __restrict__ counts, int regen_only, int t0,
                   long long ob) {
@@ -134,120 +197,202 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       return;  // nothing is written when the range does not fit
     }
   }
-  // warp-uniform task cursor: the next item of the task, its graph and position
-  long long next = 0, tend = 0;
-  bool tasks_left = true;
-  int cg = 0;
-  unsigned cu = 0, cseg = 0;  // row and segment of item `next` (its local index is next - item_begin)
-  // lane state
+  const bool rrp = P.rrp != 0 && !list_mode;
+  const bool scattered = list_mode || rrp;
+  const int wid = threadIdx.x >> 5;
+  // the warp's queue and feed (shared memory: they are touched once per item, not per iteration)
+  __shared__ WarpQueue<w_t> wqs[SAMPLER_THREADS / 32];
+  __shared__ long long s_item[SAMPLER_THREADS];  // the lane's current item
+  WarpQueue<w_t>& Q = wqs[wid];
+  if (lane == 0) {
+    Q.fnext = 0;
+    Q.fend = 0;
+    Q.tasks_left = 1;
+  }
+  __syncwarp();
+  int qn = 0, qh = 0;  // entries [qh, qn) of the queue are still to be taken (warp-uniform)
+  // ---- lane state
   bool have = false, fresh = false;
-  long long item = 0, obase = 0;
+  unsigned long long sbase = 0;  // STAGE: slot base; EMIT: output position of edge 0
+  unsigned ssize = 0;
+  long long expect = 0;
   unsigned u = 0, seg = 0, j = 0, end = 0, t = 0, k = 0;
   q_t Qprev = 0;
   typename T::lp_t Lp{};
   w_t wu = 0;
+  unsigned wprev = 0;        // integer weights: w of the last candidate (Q_prev = w_u w_prev unless capped)
   unsigned pz = 0, pw = 0;   // the lane's next draw (index t): acceptance words ...
   ff pLr{0.f, 0.f};          // ... and its -ln r_s
-  // the lane's current weight run (integer weights): candidates before run_end weigh run_w
-  unsigned run_end = 0;
+  unsigned run_end = 0;      // integer weights: candidates before run_end weigh run_w
   int run_w = 0;
-  // graph of the lane's item (batched plans only)
-  int gi_l = 0;
+  int gi_l = 0;              // graph of the lane's item (batched plans)
   const w_t* w_l = nullptr;
   q_t S_l = 0;
-  unsigned k0_l = 0, k1_l = 0;
-  unsigned long long sbase = 0;  // staging: the item's slot and its size
-  unsigned ssize = 0;
+  Keys<SINGLE> keys{};
   __shared__ unsigned sgrp[MODE == MODE_STAGE ? GROUP : 1][SAMPLER_THREADS];  // staging group, [entry][thread]
-  unsigned n_iter = 0;  // loop iterations of the lane (fallbacks and ties go straight to the stats)
+  unsigned n_iter = 0;
+  int cur_task = -1;  // the task the warp took last (per-task clock)
+  const bool clock_tasks = MODE != MODE_EMIT && P.task_ns != nullptr;
+
+  // Fills the queue with up to 32 items (fetching tasks as needed); false when none is left.
+  auto reload = [&]() -> bool {
+    long long fnext = Q.fnext, fend = Q.fend;
+    while (fnext >= fend) {
+      if (!Q.tasks_left) return false;
+      unsigned tix = 0;
+      if (lane == 0) tix = atomicAdd(P.task_ctr, 1u);
+      tix = __shfl_sync(FULL_MASK, tix, 0);
+      bool stop = false;
+      if (MODE == MODE_EMIT && list_mode) {
+        if ((long long)tix * 32 >= n_list) {
+          stop = true;
+        } else {
+          fnext = (long long)tix * 32;
+          fend = fnext + 32 < n_list ? fnext + 32 : n_list;
+        }
+      } else {
+        tix += (unsigned)t0;  // the range's first task
+        if (clock_tasks && lane == 0 && tix < (unsigned)P.T) {
+          const unsigned long long now = global_ns();
+          if (cur_task >= 0) P.task_ns[2 * cur_task + 1] = now;
+          P.task_ns[2 * tix] = now;
+        }
+        if (tix < (unsigned)P.T) cur_task = (int)tix;
+        if (rrp) {
+          if (tix >= (unsigned)P.T || (long long)tix >= P.n_items) {
+            stop = true;
+          } else {
+            if (lane == 0) Q.rtask = tix;
+            fnext = 0;
+            fend = (P.n_items - (long long)tix + P.T - 1) / P.T;
+          }
+        } else if (tix >= (unsigned)P.T || P.task_start[tix] >= ie) {
+          stop = true;
+        } else {
+          const long long a = P.task_start[tix], b = P.task_start[tix + 1];
+          fnext = a > ib ? a : ib;
+          fend = b < ie ? b : ie;
+          if (fnext < fend && lane == 0) {  // position of the task's first item (once per task)
+            const int g0 = SINGLE ? 0 : graph_of_item(P.graphs, P.G, fnext);
+            const DevGraph& g = SINGLE ? G1 : P.graphs[g0];
+            const ItemPos cp = item_pos(g, fnext - g.item_begin);
+            Q.cg = g0;
+            Q.cu = cp.u;
+            Q.cseg = cp.seg;
+          }
+        }
+      }
+      if (stop) {
+        if (lane == 0) Q.tasks_left = 0;
+        __syncwarp();
+        return false;
+      }
+      __syncwarp();
+    }
+    const long long left = fend - fnext;
+    const int avail = left < 32 ? (int)left : 32;
+    bool ok = lane < avail;
+    long long it = 0;
+    int gq = 0;
+    ItemPos ip{0, 0u, 0u};
+    if (scattered) {
+      if (ok) {
+        it = (MODE == MODE_EMIT && list_mode) ? P.ovf_list[fnext + lane]
+                                              : (long long)Q.rtask + (fnext + lane) * (long long)P.T;
+        ok = it >= ib && it < ie;
+      }
+      if (ok) {
+        gq = SINGLE ? 0 : graph_of_item(P.graphs, P.G, it);
+        const DevGraph& g = SINGLE ? G1 : P.graphs[gq];
+        ip = item_pos(g, it - g.item_begin);
+      }
+    } else {
+      const int cg = Q.cg;
+      const unsigned cu = Q.cu, cseg = Q.cseg;
+      __syncwarp();  // every lane has read the cursor before lane 0 moves it
+      it = fnext + lane;
+      gq = cg;
+      ip = ItemPos{fnext - (SINGLE ? 0ll : P.graphs[cg].item_begin), cu, cseg};
+      if (SINGLE) {
+        ip = item_advance(G1, ip, ok ? lane : 0);
+      } else if (ok) {
+        cursor_advance(P.graphs, gq, ip, lane);
+      }
+      // the warp cursor moves past the queued items
+      if (fnext + avail < fend && lane == 0) {
+        int cg2 = cg;
+        ItemPos cp{fnext - (SINGLE ? 0ll : P.graphs[cg].item_begin), cu, cseg};
+        if (SINGLE)
+          cp = item_advance(G1, cp, avail);
+        else
+          cursor_advance(P.graphs, cg2, cp, avail);
+        Q.cg = cg2;
+        Q.cu = cp.u;
+        Q.cseg = cp.seg;
+      }
+    }
+    if (ok) {
+      const w_t* Wq = SINGLE ? (const w_t*)G1.w : (const w_t*)P.graphs[gq].w;
+      Q.w[lane] = __ldg(&Wq[ip.u]);
+      Q.u[lane] = ip.u;
+      Q.seg[lane] = ip.seg;
+      Q.item[lane] = it;
+      if (!SINGLE) Q.g[lane] = gq;
+      if (MODE == MODE_STAGE) {
+        Q.sb[lane] = (unsigned long long)P.slot_base[it];
+        Q.ss[lane] = slot_size(P, it);
+      }
+      if (MODE == MODE_EMIT) {
+        const long long o0 = offsets[it];
+        const long long cnt = offsets[it + 1] - o0;
+        Q.sb[lane] = (unsigned long long)(o0 - off_base);
+        Q.cnt[lane] = cnt;
+        if (regen_only && !list_mode && cnt <= (long long)slot_size(P, it)) ok = false;  // staged: copied
+      }
+    }
+    const unsigned okm = __ballot_sync(FULL_MASK, ok);
+    if (lane == 0) {
+      Q.ok = okm;
+      Q.fnext = fnext + avail;
+      Q.fend = fend;
+    }
+    __syncwarp();
+    qn = avail;
+    qh = 0;
+    return true;
+  };
 
   while (true) {
-    // ---- (1) lanes without an item take the next items of the warp's task
+    // ---- (1) lanes without an item take the next queue entries
     unsigned need = __ballot_sync(FULL_MASK, !have);
     while (need) {
-      if (next >= tend) {
-        if (!tasks_left) break;
-        unsigned tix = 0;
-        if (lane == 0) tix = atomicAdd(P.task_ctr, 1u);
-        tix = __shfl_sync(FULL_MASK, tix, 0);
-        if (MODE == MODE_EMIT && list_mode) {
-          if ((long long)tix * 32 >= n_list) {
-            tasks_left = false;
-            break;
-          }
-          next = (long long)tix * 32;
-          tend = next + 32 < n_list ? next + 32 : n_list;
-          continue;
-        }
-        tix += (unsigned)t0;  // the range's first task
-        if (tix >= (unsigned)P.T || P.task_start[tix] >= ie) {
-          tasks_left = false;
-          break;
-        }
-        long long a = P.task_start[tix], b = P.task_start[tix + 1];
-        next = a > ib ? a : ib;
-        tend = b < ie ? b : ie;
-        if (next < tend) {  // position of the task's first item (once per task, warp-uniform)
-          cg = SINGLE ? 0 : graph_of_item(P.graphs, P.G, next);
-          const DevGraph& g = SINGLE ? G1 : P.graphs[cg];
-          const ItemPos cp = item_pos(g, next - g.item_begin);
-          cu = cp.u;
-          cseg = cp.seg;
-        }
-        continue;
-      }
-      long long avail = tend - next;
-      int rank = __popc(need & lanemask_lt);
-      int taken = __popc(need);
+      if (qh >= qn && !reload()) break;
+      const int rank = __popc(need & lanemask_lt);
+      const int avail = qn - qh;
       if (!have && rank < avail) {
-        have = true;
-        fresh = true;
-        ItemPos ip{0, 0u, 0u};
-        if (MODE == MODE_EMIT && list_mode) {  // scattered items: locate each by bisection
-          item = P.ovf_list[next + rank];
-          if (item < ib || item >= ie) {
-            have = fresh = false;
-          } else {
-            gi_l = SINGLE ? 0 : graph_of_item(P.graphs, P.G, item);
-            const DevGraph& g = SINGLE ? G1 : P.graphs[gi_l];
-            ip = item_pos(g, item - g.item_begin);
-          }
-        } else {  // consecutive items: a few steps from the warp's cursor
-          item = next + rank;
-          gi_l = cg;
-          ip = ItemPos{next - (SINGLE ? 0ll : P.graphs[cg].item_begin), cu, cseg};
-          if (SINGLE)
-            ip = item_advance(G1, ip, rank);
-          else
-            cursor_advance(P.graphs, gi_l, ip, rank);
-          if (MODE == MODE_EMIT && regen_only &&
-              offsets[item + 1] - offsets[item] <= (long long)slot_size(P, item))
-            have = fresh = false;  // staged: the copy kernel wrote it
+        const int e = qh + rank;
+        if ((Q.ok >> e) & 1u) {
+          have = true;
+          fresh = true;
+          s_item[threadIdx.x] = Q.item[e];
+          u = Q.u[e];
+          seg = Q.seg[e];
+          wu = Q.w[e];
+          if (!SINGLE) gi_l = Q.g[e];
+          if (MODE != MODE_COUNT) sbase = Q.sb[e];
+          if (MODE == MODE_STAGE) ssize = Q.ss[e];
+          if (MODE == MODE_EMIT) expect = Q.cnt[e];
         }
-        u = ip.u;
-        seg = ip.seg;
       }
-      const long long adv = taken < avail ? taken : avail;
-      next += adv;
-      if (!(MODE == MODE_EMIT && list_mode) && next < tend) {
-        ItemPos cp{next - adv - (SINGLE ? 0ll : P.graphs[cg].item_begin), cu, cseg};
-        if (SINGLE)
-          cp = item_advance(G1, cp, adv);
-        else
-          cursor_advance(P.graphs, cg, cp, adv);
-        cu = cp.u;
-        cseg = cp.seg;
-      }
+      const int taken = __popc(need);
+      qh += taken < avail ? taken : avail;
       need = __ballot_sync(FULL_MASK, !have);
     }
-    if (!__any_sync(FULL_MASK, have)) {
-      if (!tasks_left) break;
-      continue;
-    }
+    if (!__any_sync(FULL_MASK, have)) break;
 
     unsigned target = 0;
     bool look = false, done = false;
-    // ---- (2) set-up of new items: bounds, graph, w_u
+    // ---- (2) set-up of new items: bounds (and the graph's constants in a batch)
     if (have && fresh) {
       unsigned j0;
       if (SINGLE) {
@@ -257,18 +402,14 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         pos_bounds(g, ItemPos{0, u, seg}, j0, end);
         w_l = (const w_t*)g.w;
         S_l = T::S(g);
-        k0_l = g.key0;
-        k1_l = g.key1;
+        if constexpr (!SINGLE) {
+          keys.k0 = g.key0;
+          keys.k1 = g.key1;
+        }
       }
-      wu = __ldg(&(SINGLE ? (const w_t*)G1.w : w_l)[u]);
       run_end = 0;  // no cached run for the new item
       t = 0;
       k = 0;
-      if (MODE == MODE_EMIT) obase = offsets[item] - off_base;
-      if (MODE == MODE_STAGE) {
-        sbase = P.slot_base[item];
-        ssize = slot_size(P, item);
-      }
       target = j0;  // first position: p = Q(j0) / S
       look = true;
     }
@@ -285,7 +426,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
         if (delta == SKIP_UNDECIDED) {
           bool tie;
           // rare: regenerate the draw's skip words rather than keep them in registers
-          const u32x4 d = philox4x32_10(u32x4{t - 1u, seg, u, 0u}, SINGLE ? G1.key0 : k0_l, SINGLE ? G1.key1 : k1_l);
+          const u32x4 d = keys.draw(G1, t - 1u, seg, u);
           delta = T::skip2(2ull * grid52(d.x, d.y) + 1ull, Qprev, S, R, &tie);
           atomicAdd(&P.stats[1], 1ull);
           if (tie) atomicAdd(&P.stats[2], 1ull);
@@ -309,7 +450,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       }
       const unsigned az = pz, aw = pw;  // acceptance words of the draw that made the candidate
       {
-        const u32x4 nb = philox4x32_10(u32x4{t, seg, u, 0u}, SINGLE ? G1.key0 : k0_l, SINGLE ? G1.key1 : k1_l);
+        const u32x4 nb = keys.draw(G1, t, seg, u);
         pz = nb.z;
         pw = nb.w;
         pLr = ff_neglog_r53(2ull * grid52(nb.x, nb.y) + 1ull);
@@ -317,10 +458,16 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       const q_t Qt = T::Q(wu, wt, S);
       // ---- (5) acceptance r_a < q / p, with the draw that made the candidate
       if (!fresh) {
-        bool acc = (Qt == Qprev) || T::accept(grid52(az, aw), Qprev, Qt);
+        bool acc;
+        if (Qt == Qprev)
+          acc = true;
+        else if (!WF && Qprev != S)
+          acc = accept_ratio(grid52(az, aw), wprev, (unsigned)wt);
+        else
+          acc = T::accept(grid52(az, aw), Qprev, Qt);
         if (acc) {
           if (MODE == MODE_EMIT) {
-            long long pos = obase + k;
+            long long pos = (long long)sbase + k;
             if (pos < capacity) {
               E e;
               e.x = u;
@@ -346,6 +493,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
           ++k;
         }
       }
+      if (!WF) wprev = (unsigned)wt;
       // ---- (6) p <- q: a new L_p when q changed (and for a new item)
       if (fresh || Qt != Qprev) {
         Qprev = Qt;
@@ -361,9 +509,9 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
     // ---- (7) item end
     if (have && done) {
       if (MODE == MODE_EMIT) {
-        long long expect = offsets[item + 1] - offsets[item];
         if ((long long)k != expect) set_error(P.err, CL_ERR_DEVICE);
       } else {
+        const long long item = s_item[threadIdx.x];
         counts[item] = (int)k;
         if (MODE == MODE_STAGE) {
           if (k <= ssize) {
@@ -386,6 +534,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, 4)
       have = false;
     }
   }
+  if (clock_tasks && lane == 0 && cur_task >= 0) P.task_ns[2 * cur_task + 1] = global_ns();
   unsigned long long n_iter64 = n_iter;
   if (MODE != MODE_EMIT) {
 #pragma unroll

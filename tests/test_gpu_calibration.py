@@ -2,7 +2,8 @@
 the GPU (through the C ABI) against the CPU oracle.
 
 Section 3 gives E[d_i] = w_i - w_i^2/S without capping; the capped form is
-E_u = sum_{v != u} min(1, w_u w_v / S).  Pins: O(n^2) brute force at n = 2000,
+E_u = sum_{v != u} min(1, w_u w_v / S).  Pins: O(n^2) brute force at n = 2000
+(forward, and the pairwise gradient),
 the O(n log n) oracle at n = 10^5 and 10^7, central finite differences of the
 loss, the brute-force gradient, convergence to 1e-9 relative, and bit-exact
 edge lists sampled from the calibrated (double) weights.
@@ -87,6 +88,37 @@ def test_adjoint_against_bruteforce_and_finite_differences():
             continue
         fd = (loss(wp) - loss(wm)) / (2 * h)
         assert abs(fd - gg[k]) < 1e-5 * (abs(gg[k]) + 1e-3 * np.max(np.abs(gg))), (k, fd, gg[k])
+
+
+def test_adjoint_n2000_against_pairwise_gradient_and_finite_differences():
+    """The calibration workload's gradient checks at n = 2000: the GPU adjoint
+    against the oracle's O(n^2) pairwise gradient, and against central
+    differences of the loss L = sum_u (E_u - d_u)^2 / d_u on 12 coordinates."""
+    d, w = capped_weights(2000, 600, 45)
+    S = oracle.weight_sum_f64(w)
+    assert w[0] * w[0] > 10 * S  # strongly capped, like the n = 10^7 calibration targets
+    E = oracle.expected_degree(w, S)
+    gE = 2 * (E - d) / d
+    gp = oracle.expected_degree_adjoint(w, gE, S, pairwise=True)
+    gg = gpu_adj(w, gE)
+    assert np.max(np.abs(gg - gp)) < 1e-10 * np.max(np.abs(gp))
+
+    def loss(x):
+        Ex = gpu_E(x)
+        return float(np.sum((Ex - d) ** 2 / d))
+
+    checked = 0
+    for k in [0, 1, 3, 10, 40, 100, 300, 700, 1000, 1500, 1900, 1999]:
+        h = 1e-6 * w[k]
+        wp, wm = w.copy(), w.copy()
+        wp[k] += h
+        wm[k] -= h
+        if not (np.all(np.diff(wp) <= 0) and np.all(np.diff(wm) <= 0)):
+            continue
+        fd = (loss(wp) - loss(wm)) / (2 * h)
+        assert abs(fd - gg[k]) < 1e-5 * (abs(gg[k]) + 1e-3 * np.max(np.abs(gg))), (k, fd, gg[k])
+        checked += 1
+    assert checked >= 8
 
 
 def test_autograd_function_backward_is_the_adjoint():

@@ -108,6 +108,9 @@ def test_output_independent_of_tuning():
     for tun in ({"tasks": 1}, {"tasks": 7}, {"tasks": 100000}, {"block": 32}, {"block": 128, "blocks_per_sm": 1},
                 {"blocks_per_sm": 2, "tasks": 333}, {"no_stage": 1}, {"partition": 1},
                 {"partition": 1, "tasks": 333},  # the paper's consecutive partition instead of Eq. 3
+                {"partition": 2}, {"partition": 2, "tasks": 333},  # round robin
+                {"partition": 2, "tasks": 333, "no_stage": 1},
+                {"partition": 2, "stage_factor": -1.0},
                 {"stage_factor": -1.0}):  # 8-entry slots: most items regenerated by cl_emit
         E, c, _ = gpu_generate(w, 3, heavy_w=500.0, **tun)
         assert np.array_equal(c, cref), tun

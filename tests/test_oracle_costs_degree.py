@@ -110,3 +110,22 @@ def test_adjoint_against_bruteforce_and_finite_differences():
         wm[k] -= h
         fd = (loss(wp, d) - loss(wm, d)) / (2 * h)
         assert abs(fd - g[k]) < 1e-5 * (abs(g[k]) + 1e-3 * np.max(np.abs(g))), (k, fd, g[k])
+
+
+def test_pairwise_adjoint_pins():
+    """The O(n^2) pairwise gradient against the O(n^3) term-by-term brute force
+    (n = 200) and the O(n log n) threshold form (n = 2000), capped pairs included."""
+    for n, dmax, seed in ((200, 100, 9), (2000, 600, 10)):
+        d = inputs.powerlaw_degrees(n, 2.1, 2, dmax, seed).astype(np.float64)
+        rng = np.random.default_rng(seed)
+        w = np.sort(d * (1 + 0.05 * rng.random(n)))[::-1].copy()
+        S = oracle.weight_sum_f64(w)
+        assert w[0] * w[0] > 4 * S  # some pairs are capped
+        E = oracle.expected_degree(w, S)
+        gE = 2 * (E - d) / d
+        gp = oracle.expected_degree_adjoint(w, gE, S, pairwise=True)
+        gf = oracle.expected_degree_adjoint(w, gE, S)
+        assert np.max(np.abs(gp - gf)) < 1e-11 * np.max(np.abs(gf)), n
+        if n <= 200:
+            gb = oracle.expected_degree_adjoint(w, gE, S, brute=True)
+            assert np.max(np.abs(gp - gb)) < 1e-11 * np.max(np.abs(gb))
