@@ -66,7 +66,8 @@ typedef enum {
   CL_ERR_TIMEOUT = 7,     /* reserved: no call of this library waits on the device */
   CL_ERR_CUDA = 8,        /* a CUDA runtime call failed */
   CL_ERR_STATE = 9,       /* call order violated (e.g. cl_count before cl_plan_build) */
-  CL_ERR_DEVICE = 10      /* a device-side consistency check failed (see cl_check) */
+  CL_ERR_DEVICE = 10,     /* a device-side consistency check failed (see cl_check) */
+  CL_ERR_STOPPED = 11     /* cl_generate_stream: the caller's sink returned non-zero */
 } cl_status;
 
 typedef enum { CL_W_I32 = 0, CL_W_F64 = 1 } cl_wtype;
@@ -103,6 +104,9 @@ typedef struct {
                           * robin (Section 4): task t holds the items t, t + T, t + 2T, ...; the
                           * last two are for comparing partitions (cl_generate_host refuses
                           * CL_PART_RRP); other values: CL_ERR_INVALID_ARG */
+  int64_t max_pool_entries; /* 0; > 0 caps the staging pool (4 bytes per entry): items whose slot
+                          * lies beyond the cap are regenerated by cl_emit (for graphs whose full
+                          * staging would not fit in device memory, e.g. with cl_generate_stream) */
 } cl_tuning;
 
 enum { CL_PART_UCP = 0, CL_PART_CP = 1, CL_PART_RRP = 2 };
@@ -275,6 +279,34 @@ cl_status cl_generate_batch(cl_plan* plan, int32_t etype, void* d_edges, int64_t
 cl_status cl_generate_host(cl_plan* plan, int32_t etype, void* h_edges, int64_t capacity, void* d_edges,
                            int32_t* d_counts, int64_t* d_offsets, int32_t chunks, int32_t copy_sms,
                            int64_t* h_total, cl_stream_t stream);
+
+/* Out-of-core delivery: Algorithm 1 over every item (Section 3), the edge
+ * list handed to the caller's sink piece by piece through a bounded ring, so
+ * that a graph larger than device and host memory can be produced (the
+ * paper's 1-billion-node, 249-billion-edge network of Section 5 is ~2 TB as
+ * int32 pairs).  Items go in consecutive ranges of Eq. 3 tasks (Section 4)
+ * whose cost is about a quarter of the ring; a range is counted and scanned
+ * (d_counts / d_offsets as by cl_count / cl_scan, for all items), then emitted
+ * into the device ring in pieces of at most ring_edges / 2 edges (more than
+ * one only when a range came out larger), each copied to the host ring and
+ * passed to sink(user, h_edges, first_edge, n_edges, item_begin, item_end):
+ * h_edges holds n_edges pairs of etype, the edges first_edge ..
+ * first_edge + n_edges - 1 of the canonical edge list, which are those of
+ * items [item_begin, item_end).  The sink runs on the calling thread, in edge
+ * order, while the next range is being counted on the GPU; the data is valid
+ * until it returns.  A non-zero return stops the generation:
+ * CL_ERR_STOPPED, *h_total = edges handed over.  d_ring: device buffer of
+ * ring_edges edges of etype; h_ring: host buffer of the same size, page-locked
+ * for full speed (both caller-owned; ring_edges >= 2).  An item with more edges
+ * than half the ring returns CL_ERR_CAPACITY.  SYNCHRONOUS; refuses
+ * CL_PART_RRP plans.  Staged plans copy from the staging pool (items whose
+ * slot lies beyond the pool are regenerated), so a plan built with no_stage or
+ * a capped pool (cl_tuning.max_pool_entries) suits graphs whose staging would not fit. */
+typedef int32_t (*cl_edge_sink)(void* user, const void* h_edges, int64_t first_edge, int64_t n_edges,
+                                int64_t item_begin, int64_t item_end);
+cl_status cl_generate_stream(cl_plan* plan, int32_t etype, void* h_ring, void* d_ring, int64_t ring_edges,
+                             int32_t* d_counts, int64_t* d_offsets, cl_edge_sink sink, void* user,
+                             int64_t* h_total, cl_stream_t stream);
 
 /* --- expected degrees and weight calibration (Section 3: E[d_i] = w_i - w_i^2/S
  *     without capping; with the cap min(1, .) of Algorithm 1,

@@ -19,10 +19,10 @@ CL_OK = 0
 STATUS_NAMES = {
     0: "CL_OK", 1: "CL_ERR_INVALID_ARG", 2: "CL_ERR_UNSORTED", 3: "CL_ERR_NONFINITE", 4: "CL_ERR_RANGE",
     5: "CL_ERR_CAPACITY", 6: "CL_ERR_WORKSPACE", 7: "CL_ERR_TIMEOUT", 8: "CL_ERR_CUDA", 9: "CL_ERR_STATE",
-    10: "CL_ERR_DEVICE",
+    10: "CL_ERR_DEVICE", 11: "CL_ERR_STOPPED",
 }
 (CL_ERR_INVALID_ARG, CL_ERR_UNSORTED, CL_ERR_NONFINITE, CL_ERR_RANGE, CL_ERR_CAPACITY, CL_ERR_WORKSPACE,
- CL_ERR_TIMEOUT, CL_ERR_CUDA, CL_ERR_STATE, CL_ERR_DEVICE) = range(1, 11)
+ CL_ERR_TIMEOUT, CL_ERR_CUDA, CL_ERR_STATE, CL_ERR_DEVICE, CL_ERR_STOPPED) = range(1, 12)
 CL_W_I32, CL_W_F64 = 0, 1
 CL_E_I32, CL_E_I64 = 0, 1
 CL_PART_UCP, CL_PART_CP, CL_PART_RRP = 0, 1, 2
@@ -42,7 +42,8 @@ class cl_graph(ctypes.Structure):
 
 class cl_tuning(ctypes.Structure):
     _fields_ = [("tasks", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("no_stage", ctypes.c_int32), ("stage_factor", ctypes.c_double), ("partition", ctypes.c_int32)]
+                ("no_stage", ctypes.c_int32), ("stage_factor", ctypes.c_double), ("partition", ctypes.c_int32),
+                ("max_pool_entries", ctypes.c_int64)]
 
 
 class cl_graph_info(ctypes.Structure):
@@ -63,6 +64,11 @@ class cl_run_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("ties", ctypes.c_int64),
                 ("error", ctypes.c_int32)]
 
+
+# cl_edge_sink: int32 (*)(void* user, const void* h_edges, int64 first_edge, int64 n_edges,
+#                        int64 item_begin, int64 item_end)
+EDGE_SINK = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_int64, ctypes.c_int64)
 
 _lib = None
 
@@ -95,6 +101,7 @@ def load_library(path: str | None = None):
         "cl_generate_batch": ([vp, i32, vp, i64, vp, vp, vp, vp, vp], i32),
         "cl_generate": ([vp, i32, vp, i64, vp, vp, vp, vp], i32),
         "cl_generate_host": ([vp, i32, vp, i64, vp, vp, vp, i32, i32, P(i64), vp], i32),
+        "cl_generate_stream": ([vp, i32, vp, vp, i64, vp, vp, EDGE_SINK, vp, P(i64), vp], i32),
         "cl_stats": ([vp, P(cl_run_stats), vp], i32),
         "cl_check": ([vp, vp], i32),
         "cl_plan_destroy": ([vp], None),
@@ -253,6 +260,32 @@ def cl_generate_host(plan, etype: int, h_edges, capacity: int, d_edges, d_counts
     st = load_library().cl_generate_host(plan, etype, _ptr(h_edges), capacity, _ptr(d_edges), _ptr(d_counts),
                                          _ptr(d_offsets), chunks, copy_sms, ctypes.byref(m), _stream(stream))
     _check(st, "cl_generate_host")
+    return m.value
+
+
+def cl_generate_stream(plan, etype: int, h_ring, d_ring, ring_edges: int, d_counts, d_offsets, sink,
+                       stream=None) -> int:
+    """Whole plan delivered piece by piece to sink(h_edges_address, first_edge, n_edges,
+    item_begin, item_end) -> bool (True stops) through a host ring and a device ring of
+    ring_edges edges each; returns m (or the edges delivered before a stop)."""
+    raised = []
+
+    def _cb(user, h, first, n, ib, ie):
+        try:
+            return 1 if sink(h, first, n, ib, ie) else 0
+        except BaseException as e:  # stops the generation; re-raised below
+            raised.append(e)
+            return 1
+
+    cb = EDGE_SINK(_cb)
+    m = ctypes.c_int64(0)
+    st = load_library().cl_generate_stream(plan, etype, _ptr(h_ring), _ptr(d_ring), ring_edges, _ptr(d_counts),
+                                           _ptr(d_offsets), cb, None, ctypes.byref(m), _stream(stream))
+    if raised:
+        raise raised[0]
+    if st == CL_ERR_STOPPED:
+        return m.value
+    _check(st, "cl_generate_stream")
     return m.value
 
 

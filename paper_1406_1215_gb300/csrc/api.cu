@@ -63,6 +63,8 @@ struct cl_plan {
   cudaStream_t aux = nullptr;  // counts the second range beside the first
   std::vector<cudaEvent_t> events;
   long long* h_ends = nullptr;  // page-locked, mapped: each chunk's edge total, for its host copy
+  long long* h_sbuf = nullptr;  // page-locked, mapped: cl_generate_stream's task slot bases and pieces
+  size_t h_sbuf_n = 0;
 };
 
 namespace {
@@ -186,6 +188,8 @@ DevPlan dev_plan(const cl_plan* p) {
   P.wf64 = p->wtype == CL_W_F64 ? 1 : 0;
   P.pool_cap = p->pool_cap;
   P.blk = p->d_blk;
+  P.pool_shift = 0;
+  P.pool_entries = p->pool_cap;
   P.rrp = p->partition == CL_PART_RRP ? 1 : 0;
   P.task_ns = p->d_task_ns;
   return P;
@@ -208,6 +212,7 @@ const char* cl_status_string(cl_status s) {
     case CL_ERR_CUDA: return "CUDA runtime error";
     case CL_ERR_STATE: return "call order violated";
     case CL_ERR_DEVICE: return "device-side consistency check failed";
+    case CL_ERR_STOPPED: return "the caller's edge sink asked to stop";
   }
   return "unknown status";
 }
@@ -380,6 +385,8 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     // edges (sum em; Cauchy-Schwarz bounds the square roots); 2^-10 em covers the FP32 costs
     double cap = em * (1.0 + 0x1p-10) + 6.0 * std::sqrt((double)items * em) + 14.0 * (double)items + 1024.0;
     p->pool_cap = (unsigned long long)cap;
+    if (tuning && tuning->max_pool_entries > 0 && p->pool_cap > (unsigned long long)tuning->max_pool_entries)
+      p->pool_cap = (unsigned long long)tuning->max_pool_entries;
   }
   // default task count: tasks of about 10^4 edges of cost (Eq. 1 with the per-item
   // constant 4), between 4 and 64 per resident warp -- fewer, larger tasks cost less
@@ -615,6 +622,239 @@ cl_status cl_check(cl_plan* p, cl_stream_t stream) {
   return (cl_status)err;
 }
 
+// The host-delivery pipeline of a plan (made on first use, freed by cl_plan_destroy):
+// a copy stream, a second counting stream, `events` events and a page-locked,
+// mapped array of CL_HOST_MAX_CHUNKS + 1 totals (*d_ends: its device address).
+static cl_status host_pipe(cl_plan* p, int events, long long** d_ends) {
+  cl_status st;
+  if (!p->side && (st = cuda_ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)))) return st;
+  if (!p->aux && (st = cuda_ok(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking)))) return st;
+  if (!p->h_ends && (st = cuda_ok(cudaHostAlloc((void**)&p->h_ends, (CL_HOST_MAX_CHUNKS + 1) * sizeof(long long),
+                                                cudaHostAllocMapped))))
+    return st;
+  if ((st = cuda_ok(cudaHostGetDevicePointer((void**)d_ends, p->h_ends, 0)))) return st;
+  while ((int)p->events.size() < events) {
+    cudaEvent_t e;
+    if ((st = cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)))) return st;
+    p->events.push_back(e);
+  }
+  return CL_OK;
+}
+
+// Reads a value a kernel stored into mapped host memory, once the event that
+// follows the kernel has completed.
+static long long read_mapped(const long long* h, cudaEvent_t after, cl_status* st) {
+  *st = cuda_ok(cudaEventSynchronize(after));
+  return *(const volatile long long*)h;
+}
+
+constexpr int STREAM_MAX_PIECES = 4096;  // pieces of one window computed at a time
+
+// Entries of each half of the staging pool used by cl_generate_stream: a multiple of
+// 8 entries (32 bytes), so that slot bases stay multiples of 8 after the shift --
+// the sampler writes staged groups as aligned 16-byte stores.
+static unsigned long long pool_half(const cl_plan* p) { return (p->pool_cap / 2) & ~7ull; }
+
+cl_status cl_generate_stream(cl_plan* p, int32_t etype, void* h_ring, void* d_ring, int64_t ring_edges,
+                             int32_t* d_counts, int64_t* d_offsets, cl_edge_sink sink, void* user, int64_t* h_total,
+                             cl_stream_t stream) {
+  if (!p || !d_offsets || !h_total || !sink || !h_ring || !d_ring) return CL_ERR_INVALID_ARG;
+  if (etype != CL_E_I32 && etype != CL_E_I64) return CL_ERR_INVALID_ARG;
+  if (ring_edges < 2) return CL_ERR_INVALID_ARG;
+  if (p->n_items > 0 && !d_counts) return CL_ERR_INVALID_ARG;
+  if (p->partition == CL_PART_RRP) return CL_ERR_INVALID_ARG;  // windows of consecutive items need Eq. 3 or CP tasks
+  if (!p->built) return CL_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cl_status st;
+  *h_total = 0;
+  const long long slot = ring_edges / 2;  // edges per half of the ring
+  const size_t esize = etype == CL_E_I32 ? 8 : 16;
+  if ((st = cuda_ok(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s)))) return st;
+  if (p->n_items == 0) return cuda_ok(cudaStreamSynchronize(s));
+  long long* d_ends = nullptr;  // (unused here: the pieces carry their offsets)
+  if ((st = host_pipe(p, 8, &d_ends))) return st;
+  const size_t need = (size_t)(p->T + 1) + 2 * (2 + 2 * (size_t)STREAM_MAX_PIECES);
+  if (p->h_sbuf_n < need) {
+    if (p->h_sbuf) cudaFreeHost(p->h_sbuf);
+    p->h_sbuf = nullptr;
+    p->h_sbuf_n = 0;
+    if ((st = cuda_ok(cudaHostAlloc((void**)&p->h_sbuf, need * sizeof(long long), cudaHostAllocMapped)))) return st;
+    p->h_sbuf_n = need;
+  }
+  long long* d_sbuf = nullptr;
+  if ((st = cuda_ok(cudaHostGetDevicePointer((void**)&d_sbuf, p->h_sbuf, 0)))) return st;
+  long long* h_sb = p->h_sbuf;  // staging slot bases at the task boundaries
+  // pieces of a window (see launch_pieces): region 0 written on the counting stream,
+  // region 1 on the caller's stream (a window with more than STREAM_MAX_PIECES pieces)
+  long long* h_pc[2] = {p->h_sbuf + (p->T + 1), p->h_sbuf + (p->T + 1) + 2 + 2 * STREAM_MAX_PIECES};
+  long long* d_pc[2] = {d_sbuf + (p->T + 1), d_sbuf + (p->T + 1) + 2 + 2 * STREAM_MAX_PIECES};
+  std::vector<long long> task(p->T + 1);
+  long long Ctot = 0;
+  if ((st = cuda_ok(cudaMemcpyAsync(task.data(), p->d_task, sizeof(long long) * (p->T + 1), cudaMemcpyDeviceToHost,
+                                    s))))
+    return st;
+  if ((st = cuda_ok(cudaMemcpyAsync(&Ctot, p->d_C + p->n_items - 1, sizeof(long long), cudaMemcpyDeviceToHost, s))))
+    return st;
+  if (p->stage) launch_gather_task_slots(p->d_slot_base, p->d_task, p->T, d_sbuf, s);
+  if ((st = last_ok())) return st;
+  if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
+  // Windows of whole tasks, counted (and staged) in one launch each, so that the longest
+  // items of a window run beside its other items: at least 8 windows, so that counting
+  // window w + 1 overlaps the delivery of window w; staged plans alternate between the
+  // two halves of the staging pool, a window holding at most half of it.
+  std::vector<long long> win{0};
+  if (p->stage) {
+    const unsigned long long H = pool_half(p);
+    const unsigned long long total = (unsigned long long)h_sb[p->T];
+    unsigned long long target = (total + 7) / 8;
+    if (target > H) target = H;
+    if (target < 1) target = 1;
+    long long a = 0;
+    while (a < p->T) {
+      long long b = a + 1;
+      while (b < p->T && (unsigned long long)(h_sb[b + 1] - h_sb[a]) <= target) ++b;
+      win.push_back(b);
+      a = b;
+    }
+  } else {
+    const long long q = (p->T + 7) / 8;
+    for (long long a = q; a < p->T; a += q) win.push_back(a);
+    win.push_back(p->T);
+  }
+  const int W = (int)win.size() - 1;
+  const DevGraph* single = p->G == 1 ? &p->dg[0] : nullptr;
+  const int grid_emit = etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64;
+  cudaStream_t cs = p->aux;  // counting stream
+  cudaEvent_t evCount[2] = {p->events[0], p->events[1]}, evDone[2] = {p->events[2], p->events[3]};
+  cudaEvent_t evB[2] = {p->events[4], p->events[5]}, evC[2] = {p->events[6], p->events[7]};
+  // the plan views of window w: pool half, regeneration-list half, separate task counters
+  auto view = [&](int w, bool counting) {
+    DevPlan V = dev_plan(p);
+    const int h = w & 1;
+    if (p->stage) {
+      const unsigned long long H = pool_half(p);
+      V.pool_shift = h_sb[win[w]] - (long long)(h * H);
+      V.pool_cap = (unsigned long long)(h + 1) * H;
+      const unsigned half = V.ovf_cap / 2 > 0 ? V.ovf_cap / 2 : 1;
+      V.ovf_list = V.ovf_list + (h ? V.ovf_cap - half : 0);
+      V.ovf_cap = half;
+      V.ovf_count = V.ovf_count + h;
+      V.overflow = V.overflow + h;
+    }
+    if (counting) V.task_ctr = V.task_ctr + 2;
+    return V;
+  };
+  cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s);
+  cudaEventRecord(evDone[0], s);  // the resets above, before the first count
+  auto count_window = [&](int w) -> cl_status {
+    const long long ib = task[win[w]], ie = task[win[w + 1]];
+    cudaStreamWaitEvent(cs, evDone[w & 1], 0);  // the window two back (same halves) is delivered
+    const DevPlan V = view(w, true);
+    if (p->stage) {
+      cudaMemsetAsync(V.overflow, 0, sizeof(int), cs);
+      cudaMemsetAsync(V.ovf_count, 0, sizeof(unsigned), cs);
+    }
+    if (ie > ib) {
+      launch_count_range(V, single, d_counts, p->stage, SampleRange{ib, ie, (int)win[w], ib}, p->block,
+                         p->grid_count, cs);
+      launch_count_scan(d_counts + ib, ie - ib, (long long*)d_offsets + ib, p->d_scan_part, cs,
+                        (const long long*)d_offsets + ib);
+    }
+    launch_pieces((const long long*)d_offsets, ib, ie, slot, d_pc[0], STREAM_MAX_PIECES, cs);
+    cudaEventRecord(evCount[w & 1], cs);
+    return last_ok();
+  };
+  // a piece whose host copy is queued: handed to the sink once the copy is done
+  struct Piece {
+    int half;
+    long long first, n, ib, ie;
+  } pend{0, 0, 0, 0, 0};
+  bool pending = false, stopped = false;
+  long long delivered = 0, emitted = 0, k = 0;
+  auto deliver = [&]() -> cl_status {
+    pending = false;
+    cl_status r = cuda_ok(cudaEventSynchronize(evC[pend.half]));
+    if (r) return r;
+    if (pend.n > 0 && sink(user, (const char*)h_ring + (size_t)pend.half * slot * esize, pend.first, pend.n, pend.ib,
+                           pend.ie) != 0)
+      stopped = true;
+    delivered += pend.n;
+    return CL_OK;
+  };
+  auto fail = [&](cl_status r) {
+    cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(p->side);
+    cudaStreamSynchronize(s);
+    return r;
+  };
+  if ((st = count_window(0))) return fail(st);
+  for (int w = 0; w < W && !stopped; ++w) {
+    const long long ib = task[win[w]], ie = task[win[w + 1]];
+    if ((st = cuda_ok(cudaEventSynchronize(evCount[w & 1])))) return fail(st);
+    // the window's pieces: end item and the offset there (first: the offset at ib)
+    std::vector<long long> ends, ends_off;
+    long long off_a = 0;
+    auto read_pieces = [&](const long long* h) {
+      const volatile long long* v = h;
+      const long long kp = v[0];
+      off_a = v[1];
+      for (long long j = 0; j < kp; ++j) {
+        ends.push_back((long long)v[2 + 2 * j]);
+        ends_off.push_back((long long)v[3 + 2 * j]);
+      }
+      return kp;
+    };
+    read_pieces(h_pc[0]);
+    if (w + 1 < W && (st = count_window(w + 1))) return fail(st);
+    cudaStreamWaitEvent(s, evCount[w & 1], 0);  // this window's counts, offsets and staging
+    const DevPlan V = view(w, false);
+    long long a = ib;
+    size_t next_end = 0;
+    while (a < ie && !stopped) {
+      if (next_end == ends.size()) {  // more pieces than computed at once: the next ones, on this stream
+        launch_pieces((const long long*)d_offsets, a, ie, slot, d_pc[1], STREAM_MAX_PIECES, s);
+        if ((st = last_ok())) return fail(st);
+        if ((st = cuda_ok(cudaStreamSynchronize(s)))) return fail(st);
+        const long long off_prev = off_a;
+        if (read_pieces(h_pc[1]) == 0) return fail(CL_ERR_CAPACITY);  // one item holds more than half the ring
+        off_a = off_prev;
+      }
+      const long long b = ends[next_end];
+      const long long n_piece = ends_off[next_end] - (next_end ? ends_off[next_end - 1] : off_a);
+      if (n_piece < 0 || n_piece > slot || b <= a || b > ie) return fail(CL_ERR_DEVICE);  // inconsistent pieces
+      ++next_end;
+      const int half = (int)(k & 1);
+      void* d_half = (char*)d_ring + (size_t)half * slot * esize;
+      launch_emit(V, single, (const long long*)d_offsets, SampleRange{a, b, (int)win[w], a}, etype, d_half, slot,
+                  p->stage, p->block, grid_emit, 0, s);
+      if ((st = last_ok())) return fail(st);
+      cudaEventRecord(evB[half], s);
+      cudaStreamWaitEvent(p->side, evB[half], 0);
+      if (n_piece > 0 && (st = cuda_ok(cudaMemcpyAsync((char*)h_ring + (size_t)half * slot * esize, d_half,
+                                                       (size_t)n_piece * esize, cudaMemcpyDeviceToHost, p->side))))
+        return fail(st);
+      cudaEventRecord(evC[half], p->side);
+      if (pending && (st = deliver())) return fail(st);  // the previous piece, while this one travels
+      pend = Piece{half, emitted, n_piece, a, b};
+      pending = true;
+      emitted += n_piece;
+      a = b;
+      ++k;
+    }
+    cudaEventRecord(evDone[w & 1], s);
+  }
+  if (pending && !stopped && (st = deliver())) return fail(st);
+  if ((st = cuda_ok(cudaStreamSynchronize(p->side)))) return fail(st);
+  if ((st = cuda_ok(cudaStreamSynchronize(cs)))) return fail(st);
+  if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
+  p->staged = false;  // the pool now holds the last windows only
+  *h_total = delivered;
+  if (stopped) return CL_ERR_STOPPED;
+  int err = 0;
+  if ((st = cuda_ok(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost)))) return st;
+  return err ? (cl_status)err : CL_OK;
+}
+
 cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t capacity, void* d_edges,
                            int32_t* d_counts, int64_t* d_offsets, int32_t chunks, int32_t copy_sms, int64_t* h_total,
                            cl_stream_t stream) {
@@ -637,18 +877,8 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   if ((st = cuda_ok(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s)))) return st;
   if (p->n_items == 0) return cuda_ok(cudaStreamSynchronize(s));
   const int C = chunks == 0 ? 8 : (chunks > p->T ? p->T : chunks);
-  if (!p->side && (st = cuda_ok(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)))) return st;
-  if (!p->aux && (st = cuda_ok(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking)))) return st;
-  if (!p->h_ends && (st = cuda_ok(cudaHostAlloc((void**)&p->h_ends, (CL_HOST_MAX_CHUNKS + 1) * sizeof(long long),
-                                                cudaHostAllocMapped))))
-    return st;
   long long* d_ends = nullptr;
-  if ((st = cuda_ok(cudaHostGetDevicePointer((void**)&d_ends, p->h_ends, 0)))) return st;
-  while ((int)p->events.size() < C + 3) {
-    cudaEvent_t e;
-    if ((st = cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)))) return st;
-    p->events.push_back(e);
-  }
+  if ((st = host_pipe(p, C + 3, &d_ends))) return st;
   // chunk c: tasks [tc_c, tc_{c+1}) of Eq. 3 (equal cost), items [task_start[tc_c], task_start[tc_{c+1}])
   std::vector<int> tc(C + 1);
   std::vector<long long> ic(C + 1);
@@ -781,6 +1011,7 @@ void cl_plan_destroy(cl_plan* p) {
   }
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   if (p->h_ends) cudaFreeHost(p->h_ends);
+  if (p->h_sbuf) cudaFreeHost(p->h_sbuf);
   delete p;
 }
 

@@ -232,6 +232,9 @@ struct DevPlan {
   unsigned* pool;               // staging pool of destination nodes
   unsigned long long pool_cap;  // its entries: a slot ending past them counts as size 0 (never staged)
   const long long* slot_base;   // per item: first pool entry of its slot (n_items + 1 entries)
+  unsigned long long pool_entries;  // allocated pool entries (pool_cap may be a window's lower limit)
+  long long pool_shift;         // item i's slot sits at pool entry slot_base[i] - pool_shift (0 except
+                                // for the windows of cl_generate_stream, which reuse the pool)
   int* overflow;                // set when an item outgrew its slot
   long long* ovf_list;          // items that outgrew their slot (first ovf_cap of them)
   unsigned* ovf_count;
@@ -247,7 +250,7 @@ struct DevPlan {
 // would end past the pool).
 __device__ __forceinline__ unsigned slot_size(const DevPlan& P, long long i) {
   const long long b = P.slot_base[i + 1];
-  return (unsigned long long)b <= P.pool_cap ? (unsigned)(b - P.slot_base[i]) : 0u;
+  return (unsigned long long)(b - P.pool_shift) <= P.pool_cap ? (unsigned)(b - P.slot_base[i]) : 0u;
 }
 
 // Weight of node v of a graph with weights W and uniform-block offset bbase:
@@ -290,6 +293,18 @@ void launch_count_scan(const int* d_counts, long long n, long long* d_offsets, l
                        cudaStream_t s, const long long* d_base = nullptr);
 long long scan_partials_needed(long long n);
 void launch_copy_i64(const long long* d_src, long long* dst, cudaStream_t s);
+// *dst = the last b in [a, ie] with d_offsets[b] - d_offsets[a] <= cap
+void launch_piece_end(const long long* d_offsets, long long a, long long ie, long long cap, long long* dst,
+                      cudaStream_t s);
+// Cuts items [ib, ie) into consecutive pieces of at most cap edges: dst[0] = number of
+// pieces k (at most max_pieces; fewer when the items run out or one item alone exceeds
+// cap), dst[1] = d_offsets[ib], dst[2 + 2j] = the end item of piece j (piece j starts
+// where piece j - 1 ends), dst[3 + 2j] = d_offsets at that end.
+void launch_pieces(const long long* d_offsets, long long ib, long long ie, long long cap, long long* dst,
+                   int max_pieces, cudaStream_t s);
+// dst[t] = slot_base[task_start[t]], t = 0..T (staging slot bases at the task boundaries)
+void launch_gather_task_slots(const long long* d_slot_base, const long long* d_task_start, int T, long long* dst,
+                              cudaStream_t s);
 
 // Items [ib, ie) of a sampling launch; tasks are taken from t0 on (the first
 // task that reaches ib), and edges[0] of an emitting launch holds the first

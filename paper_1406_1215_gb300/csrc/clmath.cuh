@@ -152,8 +152,8 @@ __device__ __forceinline__ ff ff_log_tail(ff s, int e, int J) {
   ff at = ff_fast_two_sum(s.hi, ch);  // |ch| < 2^-15 |s.hi|
   at.lo = __fadd_rn(at.lo, __fadd_rn(s.lo, cl));
   const float2 t = __ldg(&CL_LNT2_FF[J - 32]);
-  const ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f((unsigned)(e - (J > 64 ? 1 : 0))));
-  return ff_sum3(le, ff{t.x, t.y}, ff{-2.0f * at.hi, -2.0f * at.lo});
+  const float2 le = __ldg(&CL_ELN2_FF[e - (J > 64 ? 1 : 0)]);  // (e or e - 1) ln2, below 53 ln2
+  return ff_sum3(ff{le.x, le.y}, ff{t.x, t.y}, ff{-2.0f * at.hi, -2.0f * at.lo});
 }
 
 // -ln r for r = A / 2^53, A odd in [1, 2^53) (Tang's reduction with a
@@ -181,8 +181,8 @@ __device__ __forceinline__ ff ff_neglog_r53(unsigned long long A) {
   const float poly = __fmul_rn(z, fmaf(z, 0.2f, 1.0f / 3.0f));
   const ff at{s.hi, fmaf(s.hi, poly, s.lo)};
   const float2 t = __ldg(&CL_LNR_FF[J - 512]);
-  const ff le = ff_mul_f(ff{CL_LN2_FF_HI, CL_LN2_FF_LO}, u23_to_f((unsigned)e));
-  return ff_sum3(le, ff{t.x, t.y}, ff{-2.0f * at.hi, -2.0f * at.lo});
+  const float2 le = __ldg(&CL_ELN2_FF[e]);  // e ln2, e <= 52
+  return ff_sum3(ff{le.x, le.y}, ff{t.x, t.y}, ff{-2.0f * at.hi, -2.0f * at.lo});
 }
 
 // -ln(1 - Q/S) = -ln(A/S), A = S - Q, for integers 0 < Q < S < 2^53; one path

@@ -1,6 +1,6 @@
 """Writes ln_tables.h: the reduction tables of the logarithms (ln(64/J) for
 J = 32..64, and for J = 65..128 ln(128/J); ln(1024/J) for J = 512..1024) and
-the atanh-series coefficients 1/(2k+1), split into float-float and
+the atanh-series coefficients 1/(2k+1) and the multiples e ln2, split into float-float and
 double-double pairs.
 
 Values come from Python's decimal module at 80 significant digits (its ln is
@@ -81,6 +81,12 @@ def main():
         lines.append(f"  {{{hexf(hi)}, {hexf(lo)}}},  // J = {J}")
     lines.append("};")
     ln2 = D(2).ln()
+    lines.append("// CL_ELN2_FF[e] = e ln2, e = 0..63, as float-float pairs (the exponent term of -ln r)")
+    lines.append("static __device__ __align__(8) float2 CL_ELN2_FF[64] = {")
+    for e in range(64):
+        hi, lo = split_ff(D(e) * ln2)
+        lines.append(f"  {{{hexf(hi)}f, {hexf(lo)}f}},")
+    lines.append("};")
     hi, lo = split_ff(ln2)
     lines.append(f"#define CL_LN2_FF_HI {hexf(hi)}f")
     lines.append(f"#define CL_LN2_FF_LO {hexf(lo)}f")

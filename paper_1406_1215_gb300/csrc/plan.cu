@@ -661,4 +661,70 @@ void launch_copy_i64(const long long* d_src, long long* dst, cudaStream_t s) {
   copy_i64_kernel<<<1, 1, 0, s>>>(d_src, dst);
 }
 
+// The end of a piece of consecutive items whose edges fit in `cap`: the last
+// b in (a, ie] with offsets[b] - offsets[a] <= cap (a itself when item a
+// alone holds more than cap edges), by binary search; stored into *out.
+__global__ void piece_end_kernel(const long long* __restrict__ offsets, long long a, long long ie, long long cap,
+                                 long long* __restrict__ out) {
+  const long long base = offsets[a];
+  long long lo = a, hi = ie;  // invariant: offsets[lo] - base <= cap
+  while (lo < hi) {
+    const long long mid = lo + (hi - lo + 1) / 2;
+    if (offsets[mid] - base <= cap)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  *out = lo;
+}
+
+void launch_piece_end(const long long* d_offsets, long long a, long long ie, long long cap, long long* dst,
+                      cudaStream_t s) {
+  piece_end_kernel<<<1, 1, 0, s>>>(d_offsets, a, ie, cap, dst);
+}
+
+// Successive piece ends by binary search, one thread (a few dozen searches):
+// out[0] = pieces k, out[1] = offsets[ib], out[2 + 2j] = end item of piece j,
+// out[3 + 2j] = offsets at that end.
+__global__ void pieces_kernel(const long long* __restrict__ offsets, long long ib, long long ie, long long cap,
+                              long long* __restrict__ out, int max_pieces) {
+  long long a = ib;
+  int k = 0;
+  out[1] = offsets[ib];
+  while (a < ie && k < max_pieces) {
+    const long long base = offsets[a];
+    long long lo = a, hi = ie;
+    while (lo < hi) {
+      const long long mid = lo + (hi - lo + 1) / 2;
+      if (offsets[mid] - base <= cap)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    if (lo == a) break;  // item a alone holds more than cap edges
+    out[2 + 2 * k] = lo;
+    out[3 + 2 * k] = offsets[lo];
+    ++k;
+    a = lo;
+  }
+  out[0] = k;
+}
+
+void launch_pieces(const long long* d_offsets, long long ib, long long ie, long long cap, long long* dst,
+                   int max_pieces, cudaStream_t s) {
+  pieces_kernel<<<1, 1, 0, s>>>(d_offsets, ib, ie, cap, dst, max_pieces);
+}
+
+__global__ void gather_task_slots_kernel(const long long* __restrict__ slot_base,
+                                         const long long* __restrict__ task_start, int T,
+                                         long long* __restrict__ out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t <= T) out[t] = slot_base[task_start[t]];
+}
+
+void launch_gather_task_slots(const long long* d_slot_base, const long long* d_task_start, int T, long long* dst,
+                              cudaStream_t s) {
+  gather_task_slots_kernel<<<(unsigned)((T + 1 + 255) / 256), 256, 0, s>>>(d_slot_base, d_task_start, T, dst);
+}
+
 }  // namespace cl

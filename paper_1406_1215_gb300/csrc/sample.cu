@@ -115,9 +115,11 @@ struct Wt<true> {
   }
 };
 
-// Philox keys of a lane's item: the precomputed round keys of a single-graph
-// plan (kernel parameter, so the key schedule costs no instruction), or the
-// seed of the lane's graph in a batch.
+// Philox draws of a lane's item: with the precomputed round keys of a
+// single-graph plan (kernel parameter, so the key schedule costs no
+// instruction), or from the seed of the lane's graph in a batch.  (Keeping the
+// item-constant part of the first two rounds per lane saves 2 of the 20 wide
+// multiplies but costs the registers that the loop needs: measured slower.)
 template <bool SINGLE>
 struct Keys;
 template <>
@@ -339,8 +341,16 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
       Q.item[lane] = it;
       if (!SINGLE) Q.g[lane] = gq;
       if (MODE == MODE_STAGE) {
-        Q.sb[lane] = (unsigned long long)P.slot_base[it];
-        Q.ss[lane] = slot_size(P, it);
+        const unsigned long long sb = (unsigned long long)(P.slot_base[it] - P.pool_shift);
+        unsigned ss = slot_size(P, it);
+        // a slot outside the pool, or not on a 32-byte boundary (the staged groups are written as
+        // aligned 16-byte stores): never staged (checked, reported)
+        if (ss > 0 && (sb + ss > P.pool_entries || (sb & 7ull) != 0)) {
+          set_error(P.err, CL_ERR_DEVICE);
+          ss = 0;
+        }
+        Q.sb[lane] = sb;
+        Q.ss[lane] = ss;
       }
       if (MODE == MODE_EMIT) {
         const long long o0 = offsets[it];
@@ -362,8 +372,66 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
     return true;
   };
 
+  bool ended = false;  // the lane's item has ended; its count and staging are written at the next step (2)
   while (true) {
-    // ---- (1) lanes without an item take the next queue entries
+    unsigned target = 0;
+    bool look = false;
+    {
+      const q_t S = SINGLE ? T::S(G1) : S_l;
+      // ---- (1) one skip for running items, with the precomputed draw t
+      if (have && !ended) {
+        ++t;
+        ++n_iter;
+        long long R = (long long)end - (long long)j;
+        long long delta = 0;
+        if (Qprev != S) {
+          delta = T::skip1(pLr, Lp, R);
+          if (delta == SKIP_UNDECIDED) {
+            bool tie;
+            // rare: regenerate the draw's skip words rather than keep them in registers
+            const u32x4 d = keys.draw(G1, t - 1u, seg, u);
+            delta = T::skip2(2ull * grid52(d.x, d.y) + 1ull, Qprev, S, R, &tie);
+            atomicAdd(&P.stats[1], 1ull);
+            if (tie) atomicAdd(&P.stats[2], 1ull);
+          }
+        }
+        if (delta >= R) {
+          ended = true;  // the candidate falls past the end of the item
+        } else {
+          target = j + (unsigned)delta;
+          look = true;
+        }
+      }
+    }
+    // ---- (2) end of the items that ended in this skip or in the last pass's look
+    if (have && ended) {
+      if (MODE == MODE_EMIT) {
+        if ((long long)k != expect) set_error(P.err, CL_ERR_DEVICE);
+      } else {
+        const long long item = s_item[threadIdx.x];
+        counts[item] = (int)k;
+        if (MODE == MODE_STAGE) {
+          if (k <= ssize) {
+            // the item's last partial group, written as a whole sector (the slot is a
+            // multiple of 8 entries, so the group lies inside it; entries past k are
+            // never read): no read-modify-write of a partial sector, no per-entry loop
+            if (k & (GROUP - 1)) {
+              uint4* dst = (uint4*)(P.pool + sbase + (k & ~(GROUP - 1)));
+              dst[0] = make_uint4(sgrp[0][threadIdx.x], sgrp[1][threadIdx.x], sgrp[2][threadIdx.x],
+                                  sgrp[3][threadIdx.x]);
+              dst[1] = make_uint4(sgrp[4][threadIdx.x], sgrp[5][threadIdx.x], sgrp[6][threadIdx.x],
+                                  sgrp[7][threadIdx.x]);
+            }
+          } else {  // remember it for the regeneration pass
+            unsigned idx = atomicAdd(P.ovf_count, 1u);
+            if (idx < P.ovf_cap) P.ovf_list[idx] = item;
+          }
+        }
+      }
+      have = false;
+      ended = false;
+    }
+    // ---- (3) lanes without an item take the next queue entries
     unsigned need = __ballot_sync(FULL_MASK, !have);
     while (need) {
       if (qh >= qn && !reload()) break;
@@ -390,9 +458,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
     }
     if (!__any_sync(FULL_MASK, have)) break;
 
-    unsigned target = 0;
-    bool look = false, done = false;
-    // ---- (2) set-up of new items: bounds (and the graph's constants in a batch)
+    // ---- (4) set-up of new items: bounds (and the graph's constants in a batch)
     if (have && fresh) {
       unsigned j0;
       if (SINGLE) {
@@ -415,32 +481,8 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
     }
     const w_t* W = SINGLE ? (const w_t*)G1.w : w_l;
     const q_t S = SINGLE ? T::S(G1) : S_l;
-    // ---- (3) one skip for running items, with the precomputed draw t
-    if (have && !fresh) {
-      ++t;
-      ++n_iter;
-      long long R = (long long)end - (long long)j;
-      long long delta = 0;
-      if (Qprev != S) {
-        delta = T::skip1(pLr, Lp, R);
-        if (delta == SKIP_UNDECIDED) {
-          bool tie;
-          // rare: regenerate the draw's skip words rather than keep them in registers
-          const u32x4 d = keys.draw(G1, t - 1u, seg, u);
-          delta = T::skip2(2ull * grid52(d.x, d.y) + 1ull, Qprev, S, R, &tie);
-          atomicAdd(&P.stats[1], 1ull);
-          if (tie) atomicAdd(&P.stats[2], 1ull);
-        }
-      }
-      if (delta >= R) {
-        done = true;  // the candidate falls past the end of the item
-      } else {
-        target = j + (unsigned)delta;
-        look = true;
-      }
-    }
     if (look) {
-      // ---- (4) weight of the candidate (or of the first position); meanwhile the next draw
+      // ---- (5) weight of the candidate (or of the first position); meanwhile the next draw
       w_t wt;
       if (WF) {
         wt = __ldg(&W[target]);
@@ -456,7 +498,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
         pLr = ff_neglog_r53(2ull * grid52(nb.x, nb.y) + 1ull);
       }
       const q_t Qt = T::Q(wu, wt, S);
-      // ---- (5) acceptance r_a < q / p, with the draw that made the candidate
+      // ---- (6) acceptance r_a < q / p, with the draw that made the candidate
       if (!fresh) {
         bool acc;
         if (Qt == Qprev)
@@ -494,44 +536,17 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
         }
       }
       if (!WF) wprev = (unsigned)wt;
-      // ---- (6) p <- q: a new L_p when q changed (and for a new item)
+      // ---- (7) p <- q: a new L_p when q changed (and for a new item)
       if (fresh || Qt != Qprev) {
         Qprev = Qt;
         if (Qt == 0)
-          done = true;  // p = 0: no further edge
+          ended = true;  // p = 0: no further edge
         else if (Qt < S)
           Lp = T::Lp(Qt, S, SINGLE ? G1.lp : P.graphs[gi_l].lp);
       }
       j = fresh ? target : target + 1;
-      if (j >= end) done = true;
+      if (j >= end) ended = true;
       fresh = false;
-    }
-    // ---- (7) item end
-    if (have && done) {
-      if (MODE == MODE_EMIT) {
-        if ((long long)k != expect) set_error(P.err, CL_ERR_DEVICE);
-      } else {
-        const long long item = s_item[threadIdx.x];
-        counts[item] = (int)k;
-        if (MODE == MODE_STAGE) {
-          if (k <= ssize) {
-            // the item's last partial group, written as a whole sector (the slot is a
-            // multiple of 8 entries, so the group lies inside it; entries past k are
-            // never read): no read-modify-write of a partial sector, no per-entry loop
-            if (k & (GROUP - 1)) {
-              uint4* dst = (uint4*)(P.pool + sbase + (k & ~(GROUP - 1)));
-              dst[0] = make_uint4(sgrp[0][threadIdx.x], sgrp[1][threadIdx.x], sgrp[2][threadIdx.x],
-                                  sgrp[3][threadIdx.x]);
-              dst[1] = make_uint4(sgrp[4][threadIdx.x], sgrp[5][threadIdx.x], sgrp[6][threadIdx.x],
-                                  sgrp[7][threadIdx.x]);
-            }
-          } else {  // remember it for the regeneration pass
-            unsigned idx = atomicAdd(P.ovf_count, 1u);
-            if (idx < P.ovf_cap) P.ovf_list[idx] = item;
-          }
-        }
-      }
-      have = false;
     }
   }
   if (clock_tasks && lane == 0 && cur_task >= 0) P.task_ns[2 * cur_task + 1] = global_ns();
@@ -583,8 +598,12 @@ __global__ void __launch_bounds__(COPY_THREADS, 8) copy_kernel(DevPlan P, long l
     if (i < ie) {
       o = offsets[i] - off_base;
       long long cc = offsets[i + 1] - offsets[i];
-      pos = P.slot_base[i];
+      pos = P.slot_base[i] - P.pool_shift;
       if (cc <= (long long)slot_size(P, i)) cnt = (int)cc;  // else: not staged, regenerated
+      if (cnt > 0 && (pos < 0 || (unsigned long long)(pos + cnt) > P.pool_entries)) {  // checked, reported
+        set_error(P.err, CL_ERR_DEVICE);
+        cnt = 0;
+      }
       if (cnt > 0) {
         int gi = g0;
         ItemPos ip = p0;

@@ -7,7 +7,7 @@ from __future__ import annotations
 import torch
 
 from . import (CL_E_I32, CL_E_I64, CL_W_F64, CL_W_I32, HEAVY_W_DEFAULT, cl_count, cl_emit, cl_generate,
-               cl_generate_batch, cl_generate_host,
+               cl_generate_batch, cl_generate_host, cl_generate_stream,
                cl_graph, cl_plan_build, cl_plan_create, cl_plan_destroy, cl_plan_graph_info, cl_plan_items,
                cl_plan_scratch_bytes, cl_plan_workspace_bytes, cl_scan, cl_stats, cl_tuning)
 
@@ -26,7 +26,7 @@ class Generator:
 
     def __init__(self, weights, seeds, heavy_w: float = HEAVY_W_DEFAULT, tasks: int = 0, block: int = 0,
                  blocks_per_sm: int = 0, no_stage: int = 0, stage_factor: float = 0.0, partition: int = 0,
-                 stream=None):
+                 max_pool_entries: int = 0, stream=None):
         if isinstance(weights, torch.Tensor):
             weights = [weights]
             seeds = [seeds]
@@ -42,7 +42,7 @@ class Generator:
         self.stream = stream
         graphs = [cl_graph(w.numel(), _wtype(w), w.data_ptr(), s & (2**64 - 1), float(heavy_w))
                   for w, s in zip(self.weights, self.seeds)]
-        tun = cl_tuning(tasks, block, blocks_per_sm, no_stage, stage_factor, partition)
+        tun = cl_tuning(tasks, block, blocks_per_sm, no_stage, stage_factor, partition, max_pool_entries)
         sb = cl_plan_scratch_bytes(self.G)
         scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
         self.plan = cl_plan_create(graphs, tun, scratch, sb, stream)
@@ -115,6 +115,32 @@ class Generator:
             raise ValueError("staging must be a device tensor shaped like out")
         self.m = cl_generate_host(self.plan, etype, out.data_ptr(), out.shape[0], None if direct else staging,
                                   self.counts, self.offsets, chunks, copy_sms, self.stream)
+        return self.m
+
+    def generate_stream(self, sink, ring_edges: int, etype: int = CL_E_I32, h_ring: torch.Tensor | None = None,
+                        d_ring: torch.Tensor | None = None) -> int:
+        """count + scan + emit delivered piece by piece: sink(pairs, first_edge, item_begin,
+        item_end) gets a host tensor view (n, 2) of the ring -- valid only during the call --
+        and returns True to stop.  The rings (ring_edges pairs, pinned on the host) are made
+        here when omitted.  Returns m (or the edges delivered before a stop)."""
+        dt = torch.int32 if etype == CL_E_I32 else torch.int64
+        if h_ring is None:
+            h_ring = torch.empty((ring_edges, 2), dtype=dt, pin_memory=True)
+        if d_ring is None:
+            d_ring = torch.empty((ring_edges, 2), dtype=dt, device=self.device)
+        if h_ring.dtype != dt or h_ring.shape != (ring_edges, 2) or h_ring.is_cuda or not h_ring.is_contiguous():
+            raise ValueError("h_ring must be a contiguous host (ring_edges, 2) tensor of the edge type")
+        if d_ring.dtype != dt or d_ring.shape != (ring_edges, 2) or not d_ring.is_cuda:
+            raise ValueError("d_ring must be a device (ring_edges, 2) tensor of the edge type")
+
+        base, pair_bytes = h_ring.data_ptr(), 2 * h_ring.element_size()
+
+        def cb(h, first, n, ib, ie):
+            k = (h - base) // pair_bytes  # the piece sits in one half of the ring
+            return sink(h_ring[k:k + n], first, ib, ie)
+
+        self.m = cl_generate_stream(self.plan, etype, h_ring, d_ring, ring_edges, self.counts, self.offsets, cb,
+                                    self.stream)
         return self.m
 
     def generate_batch(self, edges: torch.Tensor, graph_offsets: torch.Tensor, status: torch.Tensor,

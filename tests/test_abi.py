@@ -51,6 +51,13 @@ def test_host_side_argument_checks(L):
     m = ctypes.c_int64(5)
     assert L.cl_generate_host(None, 0, None, 0, None, None, None, 0, 0, ctypes.byref(m), None) == 1
     assert L.cl_generate_host(None, 0, None, 0, None, None, None, 65, 0, ctypes.byref(m), None) == 1
+    assert L.cl_generate_stream(None, 0, None, None, 0, None, None, ctypes.cast(None, P.EDGE_SINK), None,
+                                ctypes.byref(m), None) == 1
+    T = ctypes.c_int32(7)
+    assert L.cl_plan_tasks(None, ctypes.byref(T), None, None, None) == 1
+    assert L.cl_plan_task_clock(None, None) == 1
+    assert L.cl_diag_philox_rate(0, 0, None, None, None) == 1
+    assert P.cl_status_string(11).startswith("the caller's edge sink")
     assert L.cl_plan_scratch_bytes(4) > L.cl_plan_scratch_bytes(1) > 0
 
 
