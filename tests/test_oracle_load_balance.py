@@ -58,3 +58,37 @@ def test_ucp_balances_realized_work(case, P):
     # runtime proportional to cost: each part's realized work within sampling noise of its cost
     # (capped pairs make the realized work only smaller: allow 2% for them)
     assert np.all(np.abs(ucp - cost) <= 6.0 * np.sqrt(cost) + 0.02 * cost), (name, P)
+
+
+def node_costs(g: "oracle.Graph", n: int, c_items: np.ndarray) -> np.ndarray:
+    """Eq. 1 node costs c_u = e_u + 1 from the oracle's item costs (a heavy row's
+    segments summed back into its row; every item's cost carries the +1, so a row
+    of k items gets k - 1 subtracted)."""
+    rows = np.array([g.item_bounds(i)[0] for i in range(g.n_items)], dtype=np.int64)
+    c = np.bincount(rows, weights=c_items, minlength=n)
+    k = np.bincount(rows, minlength=n)
+    c = c - np.maximum(k - 1, 0)
+    c[k == 0] = 1.0  # a row without items (the last) still costs its own work
+    return c
+
+
+@pytest.mark.parametrize("P", [7, 64, 256])
+def test_lemma3_round_robin_nodes(P):
+    """Lemma 3 (RRP over nodes, Section 4): for i < j, c(V_i) >= c(V_j) (by Lemma 1) and
+    c(V_i) - c(V_j) <= e_i, plus 1 when V_j holds one node fewer (the appendix proof uses
+    that V_j's last node costs at least 1); hence below w_i + 1 <= w_0 + 1."""
+    w = inputs.powerlaw_degrees(20000, 2.1, 2, 800, 11)
+    g = oracle.Graph(w, 3)
+    n = len(w)
+    c = node_costs(g, n, g.item_costs())
+    e = c - 1.0
+    assert np.all(np.diff(c) <= 1e-9)  # Lemma 1
+    cv = np.array([c[p::P].sum() for p in range(P)])
+    size = np.array([len(range(p, n, P)) for p in range(P)])
+    assert np.all(np.diff(cv) <= 1e-6)
+    for i in range(P):
+        for j in range(i + 1, P):
+            bound = e[i] + (1.0 if size[i] > size[j] else 0.0)
+            assert cv[i] - cv[j] <= bound + 1e-6, (i, j, cv[i] - cv[j], bound)
+            assert cv[i] - cv[j] < w[i] + 1.0
+            assert cv[i] - cv[j] < w[0] + 1.0
