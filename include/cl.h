@@ -255,26 +255,26 @@ cl_status cl_generate_batch(cl_plan* plan, int32_t etype, void* d_edges, int64_t
 
 /* Count + scan + emit of the whole plan with the edge list delivered to host
  * memory h_edges (Algorithm 1's output as in cl_emit: same order and ids).
- * The items are cut into `chunks` ranges of equal Eq. 3 cost (0: 8; at most
- * CL_HOST_MAX_CHUNKS), and the host transfer of one range overlaps the
- * sampling of the next (the first two ranges, which hold the heaviest rows,
- * are counted side by side on a third stream of the plan):
- *  - d_edges != NULL (device buffer of `capacity` edges): each range is
- *    emitted into d_edges at its final offsets, and its host copy is queued
- *    on the copy engines (a second stream of the plan) while the next range
- *    is counted; the calling thread waits for each range's total before
- *    queueing its copy.  h_edges should be page-locked for full speed.
- *  - d_edges == NULL: the emitting kernels store straight into h_edges, on
- *    `copy_sms` SMs (0: 16) that the counting launch leaves free.  h_edges
- *    must then be host memory the device can address: page-locked and mapped
- *    (cudaHostAlloc; on unified-addressing systems every page-locked buffer
- *    is mapped), or any host memory where the GPU reads and writes pageable
- *    memory (a coherent CPU-GPU link); otherwise CL_ERR_INVALID_ARG.
+ *  - d_edges != NULL (device buffer of `capacity` edges): the items are cut into
+ *    at least `chunks` windows of whole Eq. 3 tasks (0: 8; at most
+ *    CL_HOST_MAX_CHUNKS; each window's staging fits in half of the plan's pool);
+ *    window w is counted and scanned on a second stream of the plan while window
+ *    w - 1 is emitted into d_edges at its final offsets and copied to h_edges at
+ *    the same offsets on a third (copy engines).  One counting launch per window
+ *    lets a window's longest items run beside its other items.  h_edges should be
+ *    page-locked for full speed.
+ *  - d_edges == NULL: the items are cut into `chunks` ranges of equal Eq. 3 cost,
+ *    and the emitting kernels store straight into h_edges, on `copy_sms` SMs (0:
+ *    16) that the counting launch leaves free.  h_edges must then be host memory
+ *    the device can address: page-locked and mapped (cudaHostAlloc; on
+ *    unified-addressing systems every page-locked buffer is mapped), or any host
+ *    memory where the GPU reads and writes pageable memory (a coherent CPU-GPU
+ *    link); otherwise CL_ERR_INVALID_ARG.
  * d_counts (n_items int32) and d_offsets (n_items + 1 int64) are caller
  * device scratch, filled as by cl_count and cl_scan.  Synchronous: returns
  * after the last edge is in host memory, with *h_total = m; m > capacity
- * returns CL_ERR_CAPACITY (ranges that do not fit are not written).  Not
- * capturable in a CUDA graph. */
+ * returns CL_ERR_CAPACITY (windows or ranges that do not fit are not written).
+ * Refuses CL_PART_RRP plans.  Not capturable in a CUDA graph. */
 #define CL_HOST_MAX_CHUNKS 64
 cl_status cl_generate_host(cl_plan* plan, int32_t etype, void* h_edges, int64_t capacity, void* d_edges,
                            int32_t* d_counts, int64_t* d_offsets, int32_t chunks, int32_t copy_sms,
@@ -397,6 +397,12 @@ cl_status cl_diag_neglog(const uint64_t* d_A, const uint64_t* d_B, int64_t count
  * d_tier[i] = 0 (float-float decided), 1 (double-double decided), 2 (tie: nearest integer). */
 cl_status cl_diag_skip(const uint64_t* d_a, const uint64_t* d_Q, const uint64_t* d_S, const int64_t* d_R,
                        int64_t count, int64_t* d_delta, int32_t* d_tier, cl_stream_t stream);
+
+/* -ln(1 - Q_i / S_i) for doubles 0 < Q_i < S_i, evaluated as the sampler does for
+ * double weights (float-float from the doubles): d_ff[2i..2i+1] = (hi, lo); NaN
+ * outside the domain. */
+cl_status cl_diag_neglog1m_f64(const double* d_Q, const double* d_S, int64_t count, float* d_ff,
+                               cl_stream_t stream);
 
 /* Throughput of the sampler's random stream on this GPU: Philox4x32-10 blocks
  * per second (into *blocks_per_s) over a grid of resident blocks, each thread

@@ -92,6 +92,7 @@ def lib():
         L.or_skip.restype = i64
         L.or_skip_x_quad.argtypes = [dbl, dbl, dbl, _P(dbl), _P(dbl)]
         L.or_neglog_ratio_quad.argtypes = [dbl, dbl, _P(dbl), _P(dbl)]
+        L.or_neglog1m_quad.argtypes = [dbl, dbl, _P(dbl), _P(dbl)]
         L.or_analyze.argtypes = [_P(_Graph), _P(_Info)]
         L.or_analyze.restype = ctypes.c_int32
         L.or_item_bounds.argtypes = [_P(_Graph), _P(_Info), i64, _P(i64), _P(u32), _P(i64), _P(i64)]
@@ -139,6 +140,13 @@ def skip(r: float, Q: float, S: float, R: int, stats: Stats | None = None) -> in
 def skip_x_quad(r: float, Q: float, S: float):
     hi, lo = ctypes.c_double(), ctypes.c_double()
     lib().or_skip_x_quad(r, Q, S, ctypes.byref(hi), ctypes.byref(lo))
+    return hi.value, lo.value
+
+
+def neglog1m_quad(Q: float, S: float):
+    """-ln(1 - Q/S) for doubles 0 < Q < S in binary128, as (hi, lo) doubles."""
+    hi, lo = ctypes.c_double(), ctypes.c_double()
+    lib().or_neglog1m_quad(Q, S, ctypes.byref(hi), ctypes.byref(lo))
     return hi.value, lo.value
 
 

@@ -103,6 +103,13 @@ void or_skip_x_quad(double r, double Q, double S, double* hi, double* lo) {
   *lo = (double)(x - (hp_t)h);
 }
 
+void or_neglog1m_quad(double Q, double S, double* hi, double* lo) {
+  hp_t y = neglog1m_q(Q, S);
+  double h = (double)y;
+  *hi = h;
+  *lo = (double)(y - (hp_t)h);
+}
+
 void or_neglog_ratio_quad(double A, double B, double* hi, double* lo) {
   hp_t a = (hp_t)A, b = (hp_t)B, y;
   if (2.0 * A >= B)

@@ -70,6 +70,8 @@ int64_t or_skip(double r, double Q, double S, int64_t R, or_stats* st);
 /* x = ln r / ln(1 - Q/S) evaluated in binary128, returned as hi + lo doubles. */
 void or_skip_x_quad(double r, double Q, double S, double* hi, double* lo);
 /* -ln(A/B) in binary128 for 0 < A <= B, returned as hi + lo doubles. */
+/* -ln(1 - Q/S) for doubles 0 < Q < S, in binary128, as a pair of doubles. */
+void or_neglog1m_quad(double Q, double S, double* hi, double* lo);
 void or_neglog_ratio_quad(double A, double B, double* hi, double* lo);
 
 int32_t or_analyze(const or_graph* g, or_info* info);

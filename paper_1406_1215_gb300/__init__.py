@@ -110,6 +110,7 @@ def load_library(path: str | None = None):
         "cl_diag_neglog": ([vp, vp, i64, vp, vp, vp], i32),
         "cl_diag_skip": ([vp, vp, vp, vp, i64, vp, vp, vp], i32),
         "cl_diag_philox_rate": ([i64, u64, vp, P(ctypes.c_double), vp], i32),
+        "cl_diag_neglog1m_f64": ([vp, vp, i64, vp, vp], i32),
         "cl_scan_noalloc": ([vp, i64, vp, vp], i32),
         "cl_expected_degree_workspace_bytes": ([i64], sz),
         "cl_expected_degree": ([vp, i64, ctypes.c_double, vp, vp, sz, vp], i32),
@@ -378,6 +379,11 @@ def cl_diag_skip(d_a, d_Q, d_S, d_R, count: int, d_delta, d_tier, stream=None):
     st = load_library().cl_diag_skip(_ptr(d_a), _ptr(d_Q), _ptr(d_S), _ptr(d_R), count, _ptr(d_delta), _ptr(d_tier),
                                      _stream(stream))
     _check(st, "cl_diag_skip")
+
+
+def cl_diag_neglog1m_f64(d_Q, d_S, count: int, d_ff, stream=None):
+    _check(load_library().cl_diag_neglog1m_f64(_ptr(d_Q), _ptr(d_S), count, _ptr(d_ff), _stream(stream)),
+           "cl_diag_neglog1m_f64")
 
 
 def cl_diag_philox_rate(iters: int, seed: int, d_sink, stream=None) -> float:

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <vector>
 
@@ -305,6 +306,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     if (f64) {
       d.S_i = 0;
       d.S_d = res[g].S_d;
+      d.lpd = lp_const_d(d.S_d);  // for the per-candidate -ln(1 - p) in float-float
       if (gs == CL_OK && !std::isfinite(d.S_d)) gs = CL_ERR_NONFINITE;
     } else {
       d.S_i = (long long)res[g].S_i;
@@ -439,6 +441,7 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   p->d_ovf_count = L.ovf_count;
   p->d_blk = L.blk;
   p->d_snap = L.snap;
+  for (int g = 0; g < p->G; ++g) p->dg[g].blkp = L.blk ? L.blk + p->dg[g].bbase : nullptr;
   cl_status st;
   if ((st = cuda_ok(cudaMemcpyAsync(L.graphs, p->dg.data(), sizeof(DevGraph) * p->G, cudaMemcpyHostToDevice, s))))
     return st;
@@ -655,6 +658,131 @@ constexpr int STREAM_MAX_PIECES = 4096;  // pieces of one window computed at a t
 // the sampler writes staged groups as aligned 16-byte stores.
 static unsigned long long pool_half(const cl_plan* p) { return (p->pool_cap / 2) & ~7ull; }
 
+// Count windows shared by cl_generate_stream and cl_generate_host: consecutive whole Eq. 3
+// tasks, each counted (and staged) in one launch on the plan's counting stream into one half
+// of the staging pool (alternating), scanned (continuing the offsets) and cut into pieces of at
+// most `cap` edges; window w + 2 reuses the halves of window w once its emits are done.
+struct Windows {
+  cl_plan* p;
+  cudaStream_t s, cs;
+  int32_t* d_counts;
+  int64_t* d_offsets;
+  long long cap;
+  std::vector<long long> task, win;
+  long long* h_sb = nullptr;
+  long long* h_pc[2] = {nullptr, nullptr};
+  long long* d_pc[2] = {nullptr, nullptr};
+  cudaEvent_t evCount[2], evDone[2];
+  int W = 0;
+
+  // min_windows windows at least; false with *st set on a CUDA error
+  cl_status setup(int min_windows) {
+    cl_status st;
+    long long* d_ends = nullptr;
+    if ((st = host_pipe(p, 8, &d_ends))) return st;
+    const size_t need = (size_t)(p->T + 1) + 2 * (2 + 2 * (size_t)STREAM_MAX_PIECES);
+    if (p->h_sbuf_n < need) {
+      if (p->h_sbuf) cudaFreeHost(p->h_sbuf);
+      p->h_sbuf = nullptr;
+      p->h_sbuf_n = 0;
+      if ((st = cuda_ok(cudaHostAlloc((void**)&p->h_sbuf, need * sizeof(long long), cudaHostAllocMapped)))) return st;
+      p->h_sbuf_n = need;
+    }
+    long long* d_sbuf = nullptr;
+    if ((st = cuda_ok(cudaHostGetDevicePointer((void**)&d_sbuf, p->h_sbuf, 0)))) return st;
+    h_sb = p->h_sbuf;  // staging slot bases at the task boundaries
+    // pieces of a window (launch_pieces): region 0 written on the counting stream, region 1
+    // on the caller's stream (a window with more than STREAM_MAX_PIECES pieces)
+    h_pc[0] = p->h_sbuf + (p->T + 1);
+    h_pc[1] = h_pc[0] + 2 + 2 * STREAM_MAX_PIECES;
+    d_pc[0] = d_sbuf + (p->T + 1);
+    d_pc[1] = d_pc[0] + 2 + 2 * STREAM_MAX_PIECES;
+    task.assign(p->T + 1, 0);
+    if ((st = cuda_ok(cudaMemcpyAsync(task.data(), p->d_task, sizeof(long long) * (p->T + 1),
+                                      cudaMemcpyDeviceToHost, s))))
+      return st;
+    if (p->stage) launch_gather_task_slots(p->d_slot_base, p->d_task, p->T, d_sbuf, s);
+    if ((st = last_ok())) return st;
+    if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
+    if (min_windows < 1) min_windows = 1;
+    win.assign(1, 0);
+    if (p->stage) {  // at most half of the pool each
+      const unsigned long long H = pool_half(p);
+      const unsigned long long total = (unsigned long long)h_sb[p->T];
+      unsigned long long target = (total + min_windows - 1) / min_windows;
+      if (target > H) target = H;
+      if (target < 1) target = 1;
+      long long a = 0;
+      while (a < p->T) {
+        long long b = a + 1;
+        while (b < p->T && (unsigned long long)(h_sb[b + 1] - h_sb[a]) <= target) ++b;
+        win.push_back(b);
+        a = b;
+      }
+    } else {
+      const long long q = (p->T + min_windows - 1) / min_windows;
+      for (long long a = q; a < p->T; a += q) win.push_back(a);
+      win.push_back(p->T);
+    }
+    W = (int)win.size() - 1;
+    cs = p->aux;
+    evCount[0] = p->events[0];
+    evCount[1] = p->events[1];
+    evDone[0] = p->events[2];
+    evDone[1] = p->events[3];
+    return CL_OK;
+  }
+  // the plan view of window w: pool half, regeneration-list half, separate task counters
+  DevPlan view(int w, bool counting) const {
+    DevPlan V = dev_plan(p);
+    const int h = w & 1;
+    if (p->stage) {
+      const unsigned long long H = pool_half(p);
+      V.pool_shift = h_sb[win[w]] - (long long)(h * H);
+      V.pool_cap = (unsigned long long)(h + 1) * H;
+      const unsigned half = V.ovf_cap / 2 > 0 ? V.ovf_cap / 2 : 1;
+      V.ovf_list = V.ovf_list + (h ? V.ovf_cap - half : 0);
+      V.ovf_cap = half;
+      V.ovf_count = V.ovf_count + h;
+      V.overflow = V.overflow + h;
+    }
+    if (counting) V.task_ctr = V.task_ctr + 2;
+    return V;
+  }
+  long long ib(int w) const { return task[win[w]]; }
+  long long ie(int w) const { return task[win[w + 1]]; }
+  cl_status count(int w) {
+    const long long b = ib(w), e = ie(w);
+    cudaStreamWaitEvent(cs, evDone[w & 1], 0);  // the window two back (same halves) is emitted
+    const DevPlan V = view(w, true);
+    if (p->stage) {
+      cudaMemsetAsync(V.overflow, 0, sizeof(int), cs);
+      cudaMemsetAsync(V.ovf_count, 0, sizeof(unsigned), cs);
+    }
+    if (e > b) {
+      launch_count_range(V, p->G == 1 ? &p->dg[0] : nullptr, d_counts, p->stage, SampleRange{b, e, (int)win[w], b},
+                         p->block, p->grid_count, cs);
+      launch_count_scan(d_counts + b, e - b, (long long*)d_offsets + b, p->d_scan_part, cs,
+                        (const long long*)d_offsets + b);
+    }
+    launch_pieces((const long long*)d_offsets, b, e, cap, d_pc[0], STREAM_MAX_PIECES, cs);
+    cudaEventRecord(evCount[w & 1], cs);
+    return last_ok();
+  }
+  // the resets made on the caller's stream happen before the first count
+  void start() {
+    cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s);
+    cudaEventRecord(evDone[0], s);
+    cudaEventRecord(evDone[1], s);
+  }
+  cl_status fail(cl_status r) {
+    cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(p->side);
+    cudaStreamSynchronize(s);
+    return r;
+  }
+};
+
 cl_status cl_generate_stream(cl_plan* p, int32_t etype, void* h_ring, void* d_ring, int64_t ring_edges,
                              int32_t* d_counts, int64_t* d_offsets, cl_edge_sink sink, void* user, int64_t* h_total,
                              cl_stream_t stream) {
@@ -671,99 +799,13 @@ cl_status cl_generate_stream(cl_plan* p, int32_t etype, void* h_ring, void* d_ri
   const size_t esize = etype == CL_E_I32 ? 8 : 16;
   if ((st = cuda_ok(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s)))) return st;
   if (p->n_items == 0) return cuda_ok(cudaStreamSynchronize(s));
-  long long* d_ends = nullptr;  // (unused here: the pieces carry their offsets)
-  if ((st = host_pipe(p, 8, &d_ends))) return st;
-  const size_t need = (size_t)(p->T + 1) + 2 * (2 + 2 * (size_t)STREAM_MAX_PIECES);
-  if (p->h_sbuf_n < need) {
-    if (p->h_sbuf) cudaFreeHost(p->h_sbuf);
-    p->h_sbuf = nullptr;
-    p->h_sbuf_n = 0;
-    if ((st = cuda_ok(cudaHostAlloc((void**)&p->h_sbuf, need * sizeof(long long), cudaHostAllocMapped)))) return st;
-    p->h_sbuf_n = need;
-  }
-  long long* d_sbuf = nullptr;
-  if ((st = cuda_ok(cudaHostGetDevicePointer((void**)&d_sbuf, p->h_sbuf, 0)))) return st;
-  long long* h_sb = p->h_sbuf;  // staging slot bases at the task boundaries
-  // pieces of a window (see launch_pieces): region 0 written on the counting stream,
-  // region 1 on the caller's stream (a window with more than STREAM_MAX_PIECES pieces)
-  long long* h_pc[2] = {p->h_sbuf + (p->T + 1), p->h_sbuf + (p->T + 1) + 2 + 2 * STREAM_MAX_PIECES};
-  long long* d_pc[2] = {d_sbuf + (p->T + 1), d_sbuf + (p->T + 1) + 2 + 2 * STREAM_MAX_PIECES};
-  std::vector<long long> task(p->T + 1);
-  long long Ctot = 0;
-  if ((st = cuda_ok(cudaMemcpyAsync(task.data(), p->d_task, sizeof(long long) * (p->T + 1), cudaMemcpyDeviceToHost,
-                                    s))))
-    return st;
-  if ((st = cuda_ok(cudaMemcpyAsync(&Ctot, p->d_C + p->n_items - 1, sizeof(long long), cudaMemcpyDeviceToHost, s))))
-    return st;
-  if (p->stage) launch_gather_task_slots(p->d_slot_base, p->d_task, p->T, d_sbuf, s);
-  if ((st = last_ok())) return st;
-  if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
-  // Windows of whole tasks, counted (and staged) in one launch each, so that the longest
-  // items of a window run beside its other items: at least 8 windows, so that counting
-  // window w + 1 overlaps the delivery of window w; staged plans alternate between the
-  // two halves of the staging pool, a window holding at most half of it.
-  std::vector<long long> win{0};
-  if (p->stage) {
-    const unsigned long long H = pool_half(p);
-    const unsigned long long total = (unsigned long long)h_sb[p->T];
-    unsigned long long target = (total + 7) / 8;
-    if (target > H) target = H;
-    if (target < 1) target = 1;
-    long long a = 0;
-    while (a < p->T) {
-      long long b = a + 1;
-      while (b < p->T && (unsigned long long)(h_sb[b + 1] - h_sb[a]) <= target) ++b;
-      win.push_back(b);
-      a = b;
-    }
-  } else {
-    const long long q = (p->T + 7) / 8;
-    for (long long a = q; a < p->T; a += q) win.push_back(a);
-    win.push_back(p->T);
-  }
-  const int W = (int)win.size() - 1;
+  // windows of at most half the pool, at least 8, so that counting window w + 1 overlaps the
+  // delivery of window w; a window's longest items run beside its other items
+  Windows Wn{p, s, nullptr, d_counts, d_offsets, slot};
+  if ((st = Wn.setup(8))) return st;
   const DevGraph* single = p->G == 1 ? &p->dg[0] : nullptr;
   const int grid_emit = etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64;
-  cudaStream_t cs = p->aux;  // counting stream
-  cudaEvent_t evCount[2] = {p->events[0], p->events[1]}, evDone[2] = {p->events[2], p->events[3]};
   cudaEvent_t evB[2] = {p->events[4], p->events[5]}, evC[2] = {p->events[6], p->events[7]};
-  // the plan views of window w: pool half, regeneration-list half, separate task counters
-  auto view = [&](int w, bool counting) {
-    DevPlan V = dev_plan(p);
-    const int h = w & 1;
-    if (p->stage) {
-      const unsigned long long H = pool_half(p);
-      V.pool_shift = h_sb[win[w]] - (long long)(h * H);
-      V.pool_cap = (unsigned long long)(h + 1) * H;
-      const unsigned half = V.ovf_cap / 2 > 0 ? V.ovf_cap / 2 : 1;
-      V.ovf_list = V.ovf_list + (h ? V.ovf_cap - half : 0);
-      V.ovf_cap = half;
-      V.ovf_count = V.ovf_count + h;
-      V.overflow = V.overflow + h;
-    }
-    if (counting) V.task_ctr = V.task_ctr + 2;
-    return V;
-  };
-  cudaMemsetAsync(p->d_stats, 0, 4 * sizeof(unsigned long long), s);
-  cudaEventRecord(evDone[0], s);  // the resets above, before the first count
-  auto count_window = [&](int w) -> cl_status {
-    const long long ib = task[win[w]], ie = task[win[w + 1]];
-    cudaStreamWaitEvent(cs, evDone[w & 1], 0);  // the window two back (same halves) is delivered
-    const DevPlan V = view(w, true);
-    if (p->stage) {
-      cudaMemsetAsync(V.overflow, 0, sizeof(int), cs);
-      cudaMemsetAsync(V.ovf_count, 0, sizeof(unsigned), cs);
-    }
-    if (ie > ib) {
-      launch_count_range(V, single, d_counts, p->stage, SampleRange{ib, ie, (int)win[w], ib}, p->block,
-                         p->grid_count, cs);
-      launch_count_scan(d_counts + ib, ie - ib, (long long*)d_offsets + ib, p->d_scan_part, cs,
-                        (const long long*)d_offsets + ib);
-    }
-    launch_pieces((const long long*)d_offsets, ib, ie, slot, d_pc[0], STREAM_MAX_PIECES, cs);
-    cudaEventRecord(evCount[w & 1], cs);
-    return last_ok();
-  };
   // a piece whose host copy is queued: handed to the sink once the copy is done
   struct Piece {
     int half;
@@ -781,16 +823,11 @@ cl_status cl_generate_stream(cl_plan* p, int32_t etype, void* h_ring, void* d_ri
     delivered += pend.n;
     return CL_OK;
   };
-  auto fail = [&](cl_status r) {
-    cudaStreamSynchronize(cs);
-    cudaStreamSynchronize(p->side);
-    cudaStreamSynchronize(s);
-    return r;
-  };
-  if ((st = count_window(0))) return fail(st);
-  for (int w = 0; w < W && !stopped; ++w) {
-    const long long ib = task[win[w]], ie = task[win[w + 1]];
-    if ((st = cuda_ok(cudaEventSynchronize(evCount[w & 1])))) return fail(st);
+  Wn.start();
+  if ((st = Wn.count(0))) return Wn.fail(st);
+  for (int w = 0; w < Wn.W && !stopped; ++w) {
+    const long long ib = Wn.ib(w), ie = Wn.ie(w);
+    if ((st = cuda_ok(cudaEventSynchronize(Wn.evCount[w & 1])))) return Wn.fail(st);
     // the window's pieces: end item and the offset there (first: the offset at ib)
     std::vector<long long> ends, ends_off;
     long long off_a = 0;
@@ -804,52 +841,100 @@ cl_status cl_generate_stream(cl_plan* p, int32_t etype, void* h_ring, void* d_ri
       }
       return kp;
     };
-    read_pieces(h_pc[0]);
-    if (w + 1 < W && (st = count_window(w + 1))) return fail(st);
-    cudaStreamWaitEvent(s, evCount[w & 1], 0);  // this window's counts, offsets and staging
-    const DevPlan V = view(w, false);
+    read_pieces(Wn.h_pc[0]);
+    if (w + 1 < Wn.W && (st = Wn.count(w + 1))) return Wn.fail(st);
+    cudaStreamWaitEvent(s, Wn.evCount[w & 1], 0);  // this window's counts, offsets and staging
+    const DevPlan V = Wn.view(w, false);
     long long a = ib;
     size_t next_end = 0;
     while (a < ie && !stopped) {
       if (next_end == ends.size()) {  // more pieces than computed at once: the next ones, on this stream
-        launch_pieces((const long long*)d_offsets, a, ie, slot, d_pc[1], STREAM_MAX_PIECES, s);
-        if ((st = last_ok())) return fail(st);
-        if ((st = cuda_ok(cudaStreamSynchronize(s)))) return fail(st);
+        launch_pieces((const long long*)d_offsets, a, ie, slot, Wn.d_pc[1], STREAM_MAX_PIECES, s);
+        if ((st = last_ok())) return Wn.fail(st);
+        if ((st = cuda_ok(cudaStreamSynchronize(s)))) return Wn.fail(st);
         const long long off_prev = off_a;
-        if (read_pieces(h_pc[1]) == 0) return fail(CL_ERR_CAPACITY);  // one item holds more than half the ring
+        if (read_pieces(Wn.h_pc[1]) == 0) return Wn.fail(CL_ERR_CAPACITY);  // one item holds more than half the ring
         off_a = off_prev;
       }
       const long long b = ends[next_end];
       const long long n_piece = ends_off[next_end] - (next_end ? ends_off[next_end - 1] : off_a);
-      if (n_piece < 0 || n_piece > slot || b <= a || b > ie) return fail(CL_ERR_DEVICE);  // inconsistent pieces
+      if (n_piece < 0 || n_piece > slot || b <= a || b > ie) return Wn.fail(CL_ERR_DEVICE);  // inconsistent pieces
       ++next_end;
       const int half = (int)(k & 1);
       void* d_half = (char*)d_ring + (size_t)half * slot * esize;
-      launch_emit(V, single, (const long long*)d_offsets, SampleRange{a, b, (int)win[w], a}, etype, d_half, slot,
+      launch_emit(V, single, (const long long*)d_offsets, SampleRange{a, b, (int)Wn.win[w], a}, etype, d_half, slot,
                   p->stage, p->block, grid_emit, 0, s);
-      if ((st = last_ok())) return fail(st);
+      if ((st = last_ok())) return Wn.fail(st);
       cudaEventRecord(evB[half], s);
       cudaStreamWaitEvent(p->side, evB[half], 0);
       if (n_piece > 0 && (st = cuda_ok(cudaMemcpyAsync((char*)h_ring + (size_t)half * slot * esize, d_half,
                                                        (size_t)n_piece * esize, cudaMemcpyDeviceToHost, p->side))))
-        return fail(st);
+        return Wn.fail(st);
       cudaEventRecord(evC[half], p->side);
-      if (pending && (st = deliver())) return fail(st);  // the previous piece, while this one travels
+      if (pending && (st = deliver())) return Wn.fail(st);  // the previous piece, while this one travels
       pend = Piece{half, emitted, n_piece, a, b};
       pending = true;
       emitted += n_piece;
       a = b;
       ++k;
     }
-    cudaEventRecord(evDone[w & 1], s);
+    cudaEventRecord(Wn.evDone[w & 1], s);
   }
-  if (pending && !stopped && (st = deliver())) return fail(st);
-  if ((st = cuda_ok(cudaStreamSynchronize(p->side)))) return fail(st);
-  if ((st = cuda_ok(cudaStreamSynchronize(cs)))) return fail(st);
+  if (pending && !stopped && (st = deliver())) return Wn.fail(st);
+  if ((st = cuda_ok(cudaStreamSynchronize(p->side)))) return Wn.fail(st);
+  if ((st = cuda_ok(cudaStreamSynchronize(Wn.cs)))) return Wn.fail(st);
   if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
   p->staged = false;  // the pool now holds the last windows only
   *h_total = delivered;
   if (stopped) return CL_ERR_STOPPED;
+  int err = 0;
+  if ((st = cuda_ok(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost)))) return st;
+  return err ? (cl_status)err : CL_OK;
+}
+
+// cl_generate_host through a device buffer of the whole edge list: windows counted on the
+// counting stream while the previous window is emitted at its final offsets and copied to host
+// memory at the same place (copy engines, a second stream).
+static cl_status host_windows(cl_plan* p, int32_t etype, void* h_edges, int64_t capacity, void* d_edges,
+                              int32_t* d_counts, int64_t* d_offsets, int chunks, int64_t* h_total, cudaStream_t s) {
+  cl_status st;
+  const size_t esize = etype == CL_E_I32 ? 8 : 16;
+  Windows Wn{p, s, nullptr, d_counts, d_offsets, std::numeric_limits<long long>::max()};
+  if ((st = Wn.setup(chunks))) return st;
+  const DevGraph* single = p->G == 1 ? &p->dg[0] : nullptr;
+  const int grid_emit = etype == CL_E_I32 ? p->grid_emit32 : p->grid_emit64;
+  bool over = false;
+  long long total = 0;
+  Wn.start();
+  if ((st = Wn.count(0))) return Wn.fail(st);
+  for (int w = 0; w < Wn.W; ++w) {
+    if ((st = cuda_ok(cudaEventSynchronize(Wn.evCount[w & 1])))) return Wn.fail(st);
+    const volatile long long* v = Wn.h_pc[0];
+    const long long kp = v[0], off_b = v[1];
+    const long long off_e = kp > 0 ? (long long)v[3 + 2 * (kp - 1)] : off_b;
+    total = off_e;
+    if (w + 1 < Wn.W && (st = Wn.count(w + 1))) return Wn.fail(st);
+    if (off_e > capacity) over = true;  // the counts continue, to report m
+    if (!over && off_e > off_b) {
+      cudaStreamWaitEvent(s, Wn.evCount[w & 1], 0);  // this window's counts, offsets and staging
+      launch_emit(Wn.view(w, false), single, (const long long*)d_offsets, SampleRange{Wn.ib(w), Wn.ie(w),
+                  (int)Wn.win[w], 0}, etype, d_edges, capacity, p->stage, p->block, grid_emit, 0, s);
+      if ((st = last_ok())) return Wn.fail(st);
+      cudaEventRecord(p->events[4], s);
+      cudaStreamWaitEvent(p->side, p->events[4], 0);
+      if ((st = cuda_ok(cudaMemcpyAsync((char*)h_edges + (size_t)off_b * esize, (const char*)d_edges + off_b * esize,
+                                        (size_t)(off_e - off_b) * esize, cudaMemcpyDeviceToHost, p->side))))
+        return Wn.fail(st);
+    }
+    cudaStreamWaitEvent(s, Wn.evCount[w & 1], 0);
+    cudaEventRecord(Wn.evDone[w & 1], s);
+  }
+  if ((st = cuda_ok(cudaStreamSynchronize(p->side)))) return Wn.fail(st);
+  if ((st = cuda_ok(cudaStreamSynchronize(Wn.cs)))) return Wn.fail(st);
+  if ((st = cuda_ok(cudaStreamSynchronize(s)))) return st;
+  p->staged = false;
+  *h_total = total;
+  if (over) return CL_ERR_CAPACITY;
   int err = 0;
   if ((st = cuda_ok(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost)))) return st;
   return err ? (cl_status)err : CL_OK;
@@ -876,6 +961,9 @@ cl_status cl_generate_host(cl_plan* p, int32_t etype, void* h_edges, int64_t cap
   }
   if ((st = cuda_ok(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s)))) return st;
   if (p->n_items == 0) return cuda_ok(cudaStreamSynchronize(s));
+  if (!mapped)
+    return host_windows(p, etype, h_edges, capacity, d_edges, d_counts, d_offsets, chunks == 0 ? 8 : chunks, h_total,
+                        s);
   const int C = chunks == 0 ? 8 : (chunks > p->T ? p->T : chunks);
   long long* d_ends = nullptr;
   if ((st = host_pipe(p, C + 3, &d_ends))) return st;

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "../../include/cl.h"
 
@@ -46,6 +47,46 @@ __host__ __device__ inline LpConst lp_const(unsigned long long S) {
   return c;
 }
 
+// Per-graph constants of -ln(1 - Q/S) for double weights: S's 53-bit significand
+// s_m and biased exponent s_e, cS = 64 / (s_m >> 30) in float, 1/S as a float-float
+// pair, and the series bound S_small = S 2^-12.
+struct LpConstD {
+  unsigned long long s_m;
+  int s_e;
+  float cS;
+  float iS_hi, iS_lo;
+  double S_small;
+};
+inline LpConstD lp_const_d(double S) {
+  LpConstD c{0ull, 0, 0.0f, 0.0f, 0.0f, 0.0};
+  if (!(S > 0.0) || !std::isfinite(S)) return c;
+  unsigned long long b;
+  std::memcpy(&b, &S, sizeof b);
+  c.s_e = (int)((b >> 52) & 0x7FF);
+  c.s_m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  c.cS = (float)(64.0 / (double)(c.s_m >> 30));
+  const long double iS = 1.0L / (long double)S;
+  c.iS_hi = (float)iS;
+  c.iS_lo = (float)(iS - (long double)c.iS_hi);
+  c.S_small = std::ldexp(S, -12);
+  return c;
+}
+
+// The same constants formed on the device (diagnostics; 1/S from a double division,
+// within 2^-53 of the host's).
+__device__ inline LpConstD lp_const_d_dev(double S) {
+  LpConstD c{0ull, 0, 0.0f, 0.0f, 0.0f, 0.0};
+  const unsigned long long b = (unsigned long long)__double_as_longlong(S);
+  c.s_e = (int)((b >> 52) & 0x7FF);
+  c.s_m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  c.cS = (float)(64.0 / (double)(c.s_m >> 30));
+  const double iS = 1.0 / S;
+  c.iS_hi = (float)iS;
+  c.iS_lo = (float)(iS - (double)c.iS_hi);
+  c.S_small = S * 0x1p-12;
+  return c;
+}
+
 // One graph of a plan, as the kernels see it (lives in the plan workspace).
 struct DevGraph {
   const void* w;          // device weights, sorted non-increasing
@@ -62,8 +103,10 @@ struct DevGraph {
   long long pbase;        // offset of this graph's weight prefix (n + 1 entries)
   int wtype;              // cl_wtype
   LpConst lp;             // constants of -ln(1 - Q/S) (integer weights)
+  LpConstD lpd;           // the same for double weights
   float invS_f;           // 1 / S in single precision (costs only)
   long long bbase;        // offset of this graph's entries in the uniform-block table (integer weights)
+  const unsigned long long* blkp;  // this graph's entries of that table (set by cl_plan_build)
 };
 
 // Per-graph results of the analysis kernel (scratch of cl_plan_create).
@@ -253,13 +296,13 @@ __device__ __forceinline__ unsigned slot_size(const DevPlan& P, long long i) {
   return (unsigned long long)(b - P.pool_shift) <= P.pool_cap ? (unsigned)(b - P.slot_base[i]) : 0u;
 }
 
-// Weight of node v of a graph with weights W and uniform-block offset bbase:
+// Weight of node v of a graph with weights W and uniform-block entries blk:
 // from the lane's cached run (v < run_end), else from the block table, else
 // (a block holding a change of weight) from W itself.
-__device__ __forceinline__ int block_weight(const DevPlan& P, const int* W, long long bbase, unsigned v,
+__device__ __forceinline__ int block_weight(const unsigned long long* __restrict__ blk, const int* W, unsigned v,
                                             unsigned& run_end, int& run_w) {
   if (v < run_end) return run_w;
-  const unsigned long long e = __ldg(&P.blk[bbase + (v >> BLK_SHIFT)]);
+  const unsigned long long e = __ldg(&blk[v >> BLK_SHIFT]);
   if (e == BLK_MIXED) return __ldg(&W[v]);
   run_w = (int)(unsigned)(e >> 32);
   run_end = (unsigned)e;

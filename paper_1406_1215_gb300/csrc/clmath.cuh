@@ -193,16 +193,23 @@ __device__ __forceinline__ ff ff_neglog_r53(unsigned long long A) {
 //   -ln(A/S) = e ln2 + ln(64/J) - 2 atanh(N/D).
 // For p < 1/2048 this is e = 0, J = 64, N = -64 Q: the pure atanh series,
 // with full relative precision however small p is.
+// e ln2 - ln(Ap / B) for integers Ap, B < 2^53 of the same bit length (Ap / B in
+// (1/2, 2)), e >= 0, and e >= 1 when Ap > B: J = round(64 Ap / B) from the
+// 23-bit leading part (B >> sh) and cB = 64 / (B >> sh); N = 64 Ap - J B and
+// D = 64 Ap + J B exact in 64-bit integers; the tail as described above.
+__device__ __forceinline__ ff ff_neglog_reduced(unsigned long long Ap, unsigned long long B, int e, int sh, float cB) {
+  const float q = __fmul_rn(u23_to_f((unsigned)(Ap >> sh)), cB);
+  int J = __float_as_int(__fadd_rn(q, 12582912.0f)) - 0x4B400000;  // round to nearest
+  J = J < 32 ? 32 : (J > 128 ? 128 : J);
+  const unsigned long long JB = (unsigned long long)(unsigned)J * B;
+  const unsigned long long A64 = Ap << 6;
+  return ff_log_tail(ff_div(ff_from_i64((long long)(A64 - JB)), ff_from_u64(A64 + JB)), e, J);
+}
+
 __device__ __forceinline__ ff ff_neglog1m_table(unsigned long long Q, unsigned long long S, const LpConst& c) {
   const unsigned long long A = S - Q;
   const int e = __clzll(A) - c.zS;
-  const unsigned long long Ap = A << e;
-  const float q = __fmul_rn(u23_to_f((unsigned)(Ap >> c.sh)), c.cS);
-  int J = __float_as_int(__fadd_rn(q, 12582912.0f)) - 0x4B400000;  // round to nearest
-  J = J < 32 ? 32 : (J > 128 ? 128 : J);
-  const unsigned long long JS = (unsigned long long)(unsigned)J * S;
-  const unsigned long long A64 = Ap << 6;
-  return ff_log_tail(ff_div(ff_from_i64((long long)(A64 - JS)), ff_from_u64(A64 + JS)), e, J);
+  return ff_neglog_reduced(A << e, S, e, c.sh, c.cS);
 }
 
 // ------------------------------------------------------------- double-double
@@ -321,6 +328,24 @@ __device__ __forceinline__ long long floor_decide_ff(ff x, long long R) {
     k += (long long)(__float_as_int(tl) - 0x4B400000);
   }
   return k < R ? k : R;
+}
+
+// floor_decide_ff for 1 <= R < 2^31 on 32-bit integers: x_hi < 2^23, nearly every
+// skip, is decided here; larger x takes the 64-bit path.
+__device__ __forceinline__ int floor_decide_ff32(ff x, int R) {
+  if (x.hi < 0x1p23f) {
+    const float margin = 0x1p-40f * x.hi;
+    const float t = __fadd_rd(x.hi, 0x1p23f);  // 2^23 + floor(hi), exact
+    int k = __float_as_int(t) - 0x4B000000;
+    if (__fsub_rn(t, 0x1p23f) == x.hi) {  // hi is an integer
+      if (x.lo < -margin)
+        k -= 1;
+      else if (!(x.lo > margin))
+        return (int)SKIP_UNDECIDED;
+    }
+    return k < R ? k : R;
+  }
+  return (int)floor_decide_ff(x, (long long)R);
 }
 
 // Same for double-double with tau = 2^-92 (the tier's evaluation error is below
@@ -457,6 +482,40 @@ __device__ __forceinline__ ff ff_neglog1m(unsigned long long Q, unsigned long lo
     return ff_neglog1m_series(ff_mul(q, ff{c.iS_hi, c.iS_lo}));
   }
   return ff_neglog1m_table(Q, S, c);
+}
+
+// A positive normal double as float-float: its 53-bit significand m = 1.f 2^52
+// cut into the leading 24 bits (hi, exact) and the next 23 (lo, exact), the last
+// 6 bits dropped: relative error below 2^-47.  Requires the binary exponent E
+// (x = m 2^(E - 52)) in [-80, 100], so that hi and lo are normal floats.
+__device__ __forceinline__ ff ff_from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF) - 1023;
+  const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  const float hi = __int_as_float((unsigned)((E + 127) << 23) | (unsigned)((m >> 29) & 0x7FFFFFu));
+  const float scale = __int_as_float((unsigned)((E - 46 + 127) << 23));  // 2^(E - 46)
+  return ff{hi, __fmul_rn(u23_to_f((unsigned)(m >> 6) & 0x7FFFFFu), scale)};
+}
+
+// -ln(1 - Q/S) for doubles 0 < Q < S (double weights): the series of
+// ff_neglog1m_series for p < 2^-12 with p = Q (1/S) (Q from its leading 47
+// significand bits, 1/S a float-float pair: relative error ~2^-46); otherwise
+// the reduced logarithm of A / S, A = S - Q rounded once (2^-53), from the two
+// significands and the exponent difference.  Outside the float range of the
+// series' conversion (Q below 2^-80 or above 2^100) the double logarithm is used.
+__device__ __forceinline__ ff ff_neglog1m_d(double Q, double S, const LpConstD& c) {
+  if (Q < c.S_small) {
+    const int E = (int)(((unsigned long long)__double_as_longlong(Q) >> 52) & 0x7FF) - 1023;
+    if (E >= -80 && E <= 100) return ff_neglog1m_series(ff_mul(ff_from_double(Q), ff{c.iS_hi, c.iS_lo}));
+    const double L = d_neglog1m(Q, S);
+    const float h = (float)L;
+    return ff{h, (float)(L - (double)h)};
+  }
+  const double A = S - Q;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(A);
+  const int e = c.s_e - (int)((b >> 52) & 0x7FF);  // >= 0: A < S
+  const unsigned long long a = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  return ff_neglog_reduced(a, c.s_m, e, 30, c.cS);
 }
 
 }  // namespace cl

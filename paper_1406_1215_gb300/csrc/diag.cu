@@ -67,7 +67,9 @@ __global__ void diag_skip_kernel(const unsigned long long* __restrict__ a, const
   unsigned long long Ar = 2ull * a[i] + 1ull;
   ff Lr = ff_neglog_r53(Ar);
   ff Lp = ff_neglog1m(Q[i], S[i], lp_const(S[i]));
-  long long d = floor_decide_ff(ff_div(Lr, Lp), R[i]);
+  // the sampler's decision (32-bit below 2^31, as in sample_kernel)
+  long long d = R[i] < (1ll << 31) ? (long long)floor_decide_ff32(ff_div(Lr, Lp), (int)R[i])
+                                   : floor_decide_ff(ff_div(Lr, Lp), R[i]);
   int tr = 0;
   if (d == SKIP_UNDECIDED) {
     bool tie;
@@ -76,6 +78,21 @@ __global__ void diag_skip_kernel(const unsigned long long* __restrict__ a, const
   }
   delta[i] = d;
   tier[i] = tr;
+}
+
+// -ln(1 - Q/S) for doubles 0 < Q < S as the sampler evaluates it for double weights
+// (float-float from the doubles).
+__global__ void diag_neglog1m_f64_kernel(const double* __restrict__ Q, const double* __restrict__ S, long long n,
+                                         float* __restrict__ out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!(Q[i] > 0.0 && Q[i] < S[i] && S[i] < 1e300)) {
+    out[2 * i] = out[2 * i + 1] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const ff r = ff_neglog1m_d(Q[i], S[i], lp_const_d_dev(S[i]));
+  out[2 * i] = r.hi;
+  out[2 * i + 1] = r.lo;
 }
 
 // Philox4x32-10 throughput: every thread runs `iters` blocks, each keyed by
@@ -165,5 +182,13 @@ extern "C" cl_status cl_diag_skip(const uint64_t* d_a, const uint64_t* d_Q, cons
   diag_skip_kernel<<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
       (const unsigned long long*)d_a, (const unsigned long long*)d_Q, (const unsigned long long*)d_S,
       (const long long*)d_R, count, (long long*)d_delta, d_tier);
+  return diag_done();
+}
+
+extern "C" cl_status cl_diag_neglog1m_f64(const double* d_Q, const double* d_S, int64_t count, float* d_ff,
+                                          cl_stream_t stream) {
+  if (count < 0 || (count > 0 && (!d_Q || !d_S || !d_ff))) return CL_ERR_INVALID_ARG;
+  if (count == 0) return CL_OK;
+  diag_neglog1m_f64_kernel<<<(unsigned)((count + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_Q, d_S, count, d_ff);
   return diag_done();
 }

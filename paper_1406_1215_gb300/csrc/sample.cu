@@ -81,10 +81,8 @@ struct Wt<false> {
     q_t q = (q_t)((long long)a * (long long)b);
     return q < S ? q : S;
   }
-  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, const LpConst& c) { return ff_neglog1m(Q, S, c); }
-  static __device__ __forceinline__ long long skip1(ff Lr, lp_t Lp, long long R) {
-    return floor_decide_ff(ff_div(Lr, Lp), R);
-  }
+  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, const DevGraph& g) { return ff_neglog1m(Q, S, g.lp); }
+  static __device__ __forceinline__ int skip1(ff Lr, lp_t Lp, int R) { return floor_decide_ff32(ff_div(Lr, Lp), R); }
   static __device__ __forceinline__ long long skip2(unsigned long long Ar, q_t Q, q_t S, long long R, bool* tie) {
     return skip_fallback_dd(Ar, S - Q, S, R, tie);
   }
@@ -96,16 +94,16 @@ template <>
 struct Wt<true> {
   using w_t = double;
   using q_t = double;
-  using lp_t = double;
+  using lp_t = ff;
   static __device__ __forceinline__ q_t S(const DevGraph& g) { return g.S_d; }
   static __device__ __forceinline__ q_t Q(w_t a, w_t b, q_t S) {
     q_t q = a * b;
     return q >= S ? S : q;  // capped iff the rounded product reaches S
   }
-  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, const LpConst&) { return d_neglog1m(Q, S); }
-  static __device__ __forceinline__ long long skip1(ff Lr, lp_t Lp, long long R) {
-    return floor_decide_d(((double)Lr.hi + (double)Lr.lo) / Lp, R);
-  }
+  // float-float from the doubles (tier 1 as for integer weights; the double-double tier
+  // below decides what the 2^-40 window leaves open)
+  static __device__ __forceinline__ lp_t Lp(q_t Q, q_t S, const DevGraph& g) { return ff_neglog1m_d(Q, S, g.lpd); }
+  static __device__ __forceinline__ int skip1(ff Lr, lp_t Lp, int R) { return floor_decide_ff32(ff_div(Lr, Lp), R); }
   static __device__ __forceinline__ long long skip2(unsigned long long Ar, q_t Q, q_t S, long long R, bool* tie) {
     return skip_fallback_dd_f64(Ar, Q, S, R, tie);
   }
@@ -382,15 +380,15 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
       if (have && !ended) {
         ++t;
         ++n_iter;
-        long long R = (long long)end - (long long)j;
-        long long delta = 0;
+        const int R = (int)(end - j);  // >= 1; end <= n < 2^31
+        int delta = 0;
         if (Qprev != S) {
           delta = T::skip1(pLr, Lp, R);
-          if (delta == SKIP_UNDECIDED) {
+          if (delta == (int)SKIP_UNDECIDED) {
             bool tie;
             // rare: regenerate the draw's skip words rather than keep them in registers
             const u32x4 d = keys.draw(G1, t - 1u, seg, u);
-            delta = T::skip2(2ull * grid52(d.x, d.y) + 1ull, Qprev, S, R, &tie);
+            delta = (int)T::skip2(2ull * grid52(d.x, d.y) + 1ull, Qprev, S, R, &tie);
             atomicAdd(&P.stats[1], 1ull);
             if (tie) atomicAdd(&P.stats[2], 1ull);
           }
@@ -487,8 +485,8 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
       if (WF) {
         wt = __ldg(&W[target]);
       } else {  // integer weights: uniform-block table, the lane's current run as a cache
-        const long long bbase = SINGLE ? G1.bbase : P.graphs[gi_l].bbase;
-        wt = (w_t)block_weight(P, (const int*)W, bbase, target, run_end, run_w);
+        const unsigned long long* blk = SINGLE ? G1.blkp : P.graphs[gi_l].blkp;
+        wt = (w_t)block_weight(blk, (const int*)W, target, run_end, run_w);
       }
       const unsigned az = pz, aw = pw;  // acceptance words of the draw that made the candidate
       {
@@ -542,7 +540,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
         if (Qt == 0)
           ended = true;  // p = 0: no further edge
         else if (Qt < S)
-          Lp = T::Lp(Qt, S, SINGLE ? G1.lp : P.graphs[gi_l].lp);
+          Lp = T::Lp(Qt, S, SINGLE ? G1 : P.graphs[gi_l]);
       }
       j = fresh ? target : target + 1;
       if (j >= end) ended = true;

@@ -64,6 +64,25 @@ def test_generate_double_weights():
     assert np.array_equal(one_call(w, 4), oracle_edges(w, 4))
 
 
+def test_generate_batch_double_weights():
+    # several graphs of double weights in one plan (the batched sampler with per-lane keys and
+    # the float-float ln(1 - p) from doubles), each against the oracle
+    lib()
+    from paper_1406_1215_gb300.generator import Generator
+
+    ws = [np.sort(inputs.powerlaw_degrees(n, 2.2, 2, max(3, int(n ** 0.5)), 70 + n % 5).astype(np.float64) *
+                  (1.0 + 0.3 * (n % 3)))[::-1].copy() for n in (3000, 40000, 2, 25000)]
+    seeds = [11, 12, 13, 14]
+    g = Generator([cuda(w) for w in ws], seeds)
+    E = g.generate().cpu().numpy().astype(np.int64)
+    off = g.offsets.cpu().numpy()
+    infos = [g.info(i) for i in range(len(ws))]
+    g.close()
+    for w, s, inf in zip(ws, seeds, infos):
+        a, b = inf["item_begin"], inf["item_begin"] + inf["n_items"]
+        assert np.array_equal(E[off[a]:off[b]], oracle_edges(w, s))
+
+
 @pytest.mark.parametrize("partition", [0, 1])
 def test_generate_batch_matches_singles(partition):
     # partition 1: the consecutive partition over the graphs' concatenated nodes

@@ -143,3 +143,40 @@ def test_skip_two_tier_matches_oracle_exact_floor():
     assert not bad, bad[:10]
     assert (tg == 1).sum() > 0  # the near-boundary cases reach the double-double tier
     assert tg[-1] == 2 and dg[-1] == 53  # x = 53 exactly: tie rule gives the exact floor
+
+
+def test_neglog1m_from_doubles_against_binary128():
+    """-ln(1 - Q/S) for double weights (float-float from the doubles, the sampler's
+    tier 1) within 2^-44 relative of the oracle's binary128 value, over p from
+    1e-15 to 1 - 1e-12, both sides of the series bound p = 2^-12, and S from 1 to 1e12."""
+    P = lib()
+    import oracle
+
+    rng = np.random.default_rng(21)
+    Q, S = [], []
+    for _ in range(20000):
+        s = 10.0 ** rng.uniform(0, 12)
+        lp = rng.uniform(-15, 0)
+        p = min(10.0 ** lp, 1 - 1e-12)
+        q = s * p
+        if 0 < q < s:
+            Q.append(q)
+            S.append(s)
+    for s in (1.0, 3.0, 7.8e9, 2.5e11):  # exactly at and around the series bound
+        for p in (2.0 ** -12, 2.0 ** -12 * (1 - 2.0 ** -40), 2.0 ** -12 * (1 + 2.0 ** -40), 0.5, 1 - 2.0 ** -30):
+            if 0 < s * p < s:
+                Q.append(s * p)
+                S.append(s)
+    Qa, Sa = np.array(Q), np.array(S)
+    n = len(Qa)
+    out = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    P.cl_diag_neglog1m_f64(cuda(Qa), cuda(Sa), n, out)
+    torch.cuda.synchronize()
+    f = out.cpu().numpy().reshape(n, 2).astype(np.float64)
+    worst = 0.0
+    for i in range(n):
+        hi, lo = oracle.neglog1m_quad(float(Qa[i]), float(Sa[i]))
+        ref = hi + lo
+        err = abs((f[i, 0] - hi) + (f[i, 1] - lo)) / ref
+        worst = max(worst, err)
+    assert worst < 2.0 ** -44, worst
