@@ -185,6 +185,36 @@ __device__ __forceinline__ ff ff_neglog_r53(unsigned long long A) {
   return ff_sum3(ff{le.x, le.y}, ff{t.x, t.y}, ff{-2.0f * at.hi, -2.0f * at.lo});
 }
 
+// -ln r for r = (2k+1)/2^53 with k the top 52 bits of the word pair (hi:lo), the
+// same reduction on 32-bit pieces: A = 2k+1 = hi 2^21 + a21 with a21 = ((lo >>
+// 12) << 1) | 1 (21 bits); for hi >= 2^10 (all but 2^-22 of the draws) A' = A 2^e,
+// e = clz(hi) <= 21, has its 32 top bits t = (hi << e) | (a21 >> (21 - e)) and low
+// 21 bits l = (a21 << e) mod 2^21; J = round(A' / 2^43) = (t >> 22) + bit 21 of t;
+// N = A' - J 2^43 = Nh 2^21 + l with Nh = t - J 2^22 in [-2^21, 2^21] (wrapping
+// 32-bit arithmetic gives it exactly), which is exact as float-float.  The rest is
+// that of ff_neglog_r53; smaller hi takes ff_neglog_r53 itself.
+__device__ __forceinline__ ff ff_neglog_r53_w(unsigned lo, unsigned hi) {
+  if (hi < (1u << 10)) return ff_neglog_r53(2ull * ((((unsigned long long)hi << 32) | lo) >> 12) + 1ull);
+  const int e = __clz(hi);
+  const unsigned a21 = ((lo >> 12) << 1) | 1u;
+  const unsigned t = (hi << e) | (a21 >> (21 - e));
+  const unsigned l = (a21 << e) & 0x1FFFFFu;
+  const unsigned J = (t >> 22) + ((t >> 21) & 1u);  // in [512, 1024]
+  const int Nh = (int)(t - (J << 22));               // in [-2^21, 2^21]
+  const float nh = __fmul_rn(__fsub_rn(u23_to_f((unsigned)(Nh + (1 << 22))), 4194304.0f), 0x1p21f);  // Nh 2^21, exact
+  const ff Nf = ff_fast_two_sum(nh, u23_to_f(l));  // |nh| >= 2^21 > l, or nh = 0
+  // J 2^44 + N: the first sum is exact (|N| <= 2^42 < J 2^44), the second rounds once
+  ff Df = ff_fast_two_sum(__fmul_rn(u23_to_f(J), 0x1p44f), Nf.hi);
+  Df.lo = __fadd_rn(Df.lo, Nf.lo);
+  const ff s = ff_div(Nf, Df);
+  const float z = __fmul_rn(s.hi, s.hi);
+  const float poly = __fmul_rn(z, fmaf(z, 0.2f, 1.0f / 3.0f));
+  const ff at{s.hi, fmaf(s.hi, poly, s.lo)};
+  const float2 tb = __ldg(&CL_LNR_FF[J - 512]);
+  const float2 le = __ldg(&CL_ELN2_FF[e]);
+  return ff_sum3(ff{le.x, le.y}, ff{tb.x, tb.y}, ff{-2.0f * at.hi, -2.0f * at.lo});
+}
+
 // -ln(1 - Q/S) = -ln(A/S), A = S - Q, for integers 0 < Q < S < 2^53; one path
 // for every p (no branch on its size, so lanes of a warp stay converged):
 //   A' = A 2^e with S's leading bit, A'/S in (1/2, 2);  J = round(64 A'/S)
@@ -500,9 +530,13 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 // -ln(1 - Q/S) for doubles 0 < Q < S (double weights): the series of
 // ff_neglog1m_series for p < 2^-12 with p = Q (1/S) (Q from its leading 47
 // significand bits, 1/S a float-float pair: relative error ~2^-46); otherwise
-// the reduced logarithm of A / S, A = S - Q rounded once (2^-53), from the two
-// significands and the exponent difference.  Outside the float range of the
-// series' conversion (Q below 2^-80 or above 2^100) the double logarithm is used.
+// the reduced logarithm of A / S from the two significands and the exponent
+// difference, A = S - Q rounded to double, and the rounding error c = S - Q - A
+// (exact by Dekker's FastTwoSum, S > Q) put back to first order:
+// -ln((A + c)/S) = -ln(A/S) - c/A + O(2^-106).  Without it the 2^-53 relative
+// error of A would be 2^-53 / p of the result, 2^-41 at p = 2^-12.  Outside the
+// float range of the series' conversion (Q below 2^-80 or above 2^100) the
+// double logarithm is used.
 __device__ __forceinline__ ff ff_neglog1m_d(double Q, double S, const LpConstD& c) {
   if (Q < c.S_small) {
     const int E = (int)(((unsigned long long)__double_as_longlong(Q) >> 52) & 0x7FF) - 1023;
@@ -511,11 +545,20 @@ __device__ __forceinline__ ff ff_neglog1m_d(double Q, double S, const LpConstD& 
     const float h = (float)L;
     return ff{h, (float)(L - (double)h)};
   }
-  const double A = S - Q;
+  const double A = __dsub_rn(S, Q);
+  const double cA = __dsub_rn(__dsub_rn(S, A), Q);
   const unsigned long long b = (unsigned long long)__double_as_longlong(A);
-  const int e = c.s_e - (int)((b >> 52) & 0x7FF);  // >= 0: A < S
-  const unsigned long long a = (b & ((1ull << 52) - 1)) | (1ull << 52);
-  return ff_neglog_reduced(a, c.s_m, e, 30, c.cS);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  const int e = c.s_e - eb;  // >= 0: A < S
+  const unsigned long long a = (b & ((1ull << 52) - 1)) | (1ull << 52);  // A = a 2^(eb - 1075)
+  // c/A = (c 2^(1075 - eb)) / a with |c 2^(1075 - eb)| <= 1/2; below eb = 53 (A under
+  // 2^-970, the result above 670) the term is left out
+  const double sc = __longlong_as_double((long long)(eb >= 53 ? 2098 - eb : 0) << 52);
+  const float t = (float)__dmul_rn(cA, sc);
+  const float corr = __fmul_rn(__fmul_rn(t, 0x1p-30f), rcp_nr(u23_to_f((unsigned)(a >> 30))));
+  ff L = ff_neglog_reduced(a, c.s_m, e, 30, c.cS);
+  L.lo = __fsub_rn(L.lo, corr);
+  return L;
 }
 
 }  // namespace cl

@@ -45,7 +45,12 @@ __global__ void diag_neglog_kernel(const unsigned long long* __restrict__ A, con
     return;
   }
   // the float-float forms the sampler uses: -ln r (B = 2^53) or -ln(1 - Q/S)
-  ff f = B[i] == (1ull << 53) ? ff_neglog_r53(A[i]) : ff_neglog1m(B[i] - A[i], B[i], lp_const(B[i]));
+  // -ln r as the sampler forms it from the Philox word pair (odd A: A = 2k + 1)
+  const unsigned long long k = A[i] >> 1;
+  ff f = B[i] == (1ull << 53)
+             ? ((A[i] & 1ull) ? ff_neglog_r53_w((unsigned)((k & 0xFFFFFull) << 12), (unsigned)(k >> 20))
+                              : ff_neglog_r53(A[i]))
+             : ff_neglog1m(B[i] - A[i], B[i], lp_const(B[i]));
   dd d = dd_neglog_ratio(A[i], B[i]);
   oft[2 * i] = f.hi;
   oft[2 * i + 1] = f.lo;

@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
         const u32x4 nb = keys.draw(G1, t, seg, u);
         pz = nb.z;
         pw = nb.w;
-        pLr = ff_neglog_r53(2ull * grid52(nb.x, nb.y) + 1ull);
+        pLr = ff_neglog_r53_w(nb.x, nb.y);
       }
       const q_t Qt = T::Q(wu, wt, S);
       // ---- (6) acceptance r_a < q / p, with the draw that made the candidate

@@ -52,6 +52,16 @@ def _neglog_cases(rng):
     for edge in list(range(0, 2000)) + [2**52 - 1 - i for i in range(2000)] + [2**51 + i - 1000 for i in range(2000)]:
         A.append(2 * edge + 1)
         B.append(two53)
+    # the leading word of the pair small (2^10 <= hi < 2^32: every shift of the 32-bit
+    # reduction) and the rounding of J up to 1024
+    for j in range(29, 53):
+        for d in (0, 1, 2**8 - 1, 2**19 + 7):
+            k = (1 << j) + d if (1 << j) + d < 2**52 else (1 << j) - 1 - d
+            A.append(2 * k + 1)
+            B.append(two53)
+        kk = (1 << j) - 1  # all ones: J rounds up
+        A.append(2 * kk + 1)
+        B.append(two53)
     # L_p: A = S - Q for S up to 2^50, p from 1/S to 1 - 1/S
     for _ in range(60000):
         S = int(rng.integers(2, 2**int(rng.integers(2, 51))))
@@ -148,7 +158,8 @@ def test_skip_two_tier_matches_oracle_exact_floor():
 def test_neglog1m_from_doubles_against_binary128():
     """-ln(1 - Q/S) for double weights (float-float from the doubles, the sampler's
     tier 1) within 2^-44 relative of the oracle's binary128 value, over p from
-    1e-15 to 1 - 1e-12, both sides of the series bound p = 2^-12, and S from 1 to 1e12."""
+    1e-15 to 1 - 1e-12, both sides of the series bound p = 2^-12, and S from 1 to 1e12
+    (1e-30 to 1e30 just above the bound)."""
     P = lib()
     import oracle
 
@@ -159,6 +170,12 @@ def test_neglog1m_from_doubles_against_binary128():
         lp = rng.uniform(-15, 0)
         p = min(10.0 ** lp, 1 - 1e-12)
         q = s * p
+        if 0 < q < s:
+            Q.append(q)
+            S.append(s)
+    for _ in range(4000):  # just above the series bound, where S - Q's rounding matters most
+        s = 10.0 ** rng.uniform(-30, 30)
+        q = s * 2.0 ** -12 * (1 + rng.uniform(0, 0.01))
         if 0 < q < s:
             Q.append(q)
             S.append(s)
