@@ -37,6 +37,7 @@ struct cl_plan {
   bool tiny_slots = false;            // testing knob: 8-entry slots (most items regenerate)
   int partition = CL_PART_UCP;        // task split: Eq. 3 (default) or the consecutive partition
   unsigned ovf_cap = 1;               // regeneration list entries
+  int copy_chunk = 32;                // items per claim of the copy kernel
   // workspace (after cl_plan_build)
   bool built = false;
   size_t ws_bytes = 0;
@@ -193,6 +194,7 @@ DevPlan dev_plan(const cl_plan* p) {
   P.pool_entries = p->pool_cap;
   P.rrp = p->partition == CL_PART_RRP ? 1 : 0;
   P.task_ns = p->d_task_ns;
+  P.copy_chunk = p->copy_chunk;
   return P;
 }
 
@@ -382,6 +384,9 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
     if (S > 0) em += (S * S - res[g].S2) / (2.0 * S);
   }
   if (em < 0) em = 0;
+  // copy claims: 32 items, or 256 when items average under 8 edges (so that a claim
+  // still holds a few hundred edges and the claim counter is not the bottleneck)
+  p->copy_chunk = items > 0 && em < 8.0 * (double)items ? 256 : 32;
   if (p->stage) {
     // slots are ceil8(e + 6 sqrt(e) + 6) <= e + 6 sqrt(e) + 13 with e the item's uncapped expected
     // edges (sum em; Cauchy-Schwarz bounds the square roots); 2^-10 em covers the FP32 costs

@@ -287,6 +287,7 @@ struct DevPlan {
   int rrp;                      // round-robin partition: task t holds the items t, t + T, t + 2T, ...
   unsigned long long* task_ns;  // nullable: per task, the global timer (ns) when a warp took it and
                                 // when that warp took its next task or finished (count passes)
+  int copy_chunk;               // items per claim of the copy kernel (a multiple of 32)
 };
 
 // Staging slot of item i in entries (0: the item is never staged, its slot

@@ -560,10 +560,13 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
   }
 }
 
-// ---- copy of staged destinations.  A warp takes 32 consecutive items (one
-// per lane, pulled from a counter); their edges form one contiguous output
-// range.  Items with at least 32 staged edges are copied by the whole warp, one
-// item at a time (lane = edge); the others are flattened: the lanes cover their
+// ---- copy of staged destinations.  A warp takes a claim of consecutive items
+// from a counter (32 items, or 256 when items average under 8 edges: the small
+// graphs of a batch, 5.8e8 items, took 1.8e7 claims of 32 on one counter, whose
+// atomics alone then set the copy's time) and walks it 32 items at a time, one
+// item per lane; their edges form one contiguous output range.  Items with at
+// least 32 staged edges are copied by the whole warp, one item at a time (lane =
+// edge); the others are flattened: the lanes cover their
 // edges edge by edge (consecutive lanes write consecutive pairs), each lane
 // finding its edge's item by a 5-step search over the warp's inclusive count
 // prefix, so every load is independent of the others.  A memory-latency-bound
@@ -580,106 +583,112 @@ __global__ void __launch_bounds__(COPY_THREADS, 8) copy_kernel(DevPlan P, long l
     if (blockIdx.x == 0 && threadIdx.x == 0) set_error(P.err, CL_ERR_CAPACITY);
     return;
   }
+  const int chunk = P.copy_chunk;
   while (true) {
     unsigned c = 0;
     if (lane == 0) c = atomicAdd(P.task_ctr, 1u);
     c = __shfl_sync(FULL_MASK, c, 0);
-    long long i0 = ib + (long long)c * 32;
-    if (i0 >= ie) break;
-    long long i = i0 + lane;
-    // position of the warp's first item (warp-uniform); lanes step from it
-    const int g0 = P.G == 1 ? 0 : graph_of_item(P.graphs, P.G, i0);
-    const ItemPos p0 = item_pos(P.graphs[g0], i0 - P.graphs[g0].item_begin);
-    long long o = 0, pos = 0;
-    int cnt = 0;
-    unsigned uu = 0;
-    if (i < ie) {
-      o = offsets[i] - off_base;
-      long long cc = offsets[i + 1] - offsets[i];
-      pos = P.slot_base[i] - P.pool_shift;
-      if (cc <= (long long)slot_size(P, i)) cnt = (int)cc;  // else: not staged, regenerated
-      if (cnt > 0 && (pos < 0 || (unsigned long long)(pos + cnt) > P.pool_entries)) {  // checked, reported
-        set_error(P.err, CL_ERR_DEVICE);
-        cnt = 0;
-      }
-      if (cnt > 0) {
-        int gi = g0;
-        ItemPos ip = p0;
-        cursor_advance(P.graphs, gi, ip, lane);
-        uu = ip.u;
-      }
-    }
-    // items with at least 32 staged edges: the whole warp copies one item at a
-    // time (lane = edge, coalesced, four loads in flight per lane)
-    unsigned big = __ballot_sync(FULL_MASK, cnt >= 32);
-    while (big) {
-      const int l = __ffs(big) - 1;
-      big &= big - 1;
-      const int cl = __shfl_sync(FULL_MASK, cnt, l);
-      const long long ol = __shfl_sync(FULL_MASK, o, l);
-      const long long pl = __shfl_sync(FULL_MASK, pos, l);
-      const unsigned su = __shfl_sync(FULL_MASK, uu, l);
-      for (int e0 = lane; e0 < cl; e0 += 32 * 4) {
-        unsigned v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = e0 + 32 * q < cl ? P.pool[pl + e0 + 32 * q] : 0u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (e0 + 32 * q < cl) {
-            E pr;
-            pr.x = su;
-            pr.y = v[q];
-            edges[ol + e0 + 32 * q] = pr;
-          }
-      }
-    }
-    if (cnt >= 32) cnt = 0;  // done above; the rest are flattened edge by edge
-    int incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      int y = __shfl_up_sync(FULL_MASK, incl, d);
-      if (lane >= d) incl += y;
-    }
-    const int total = __shfl_sync(FULL_MASK, incl, 31);
-    // edges per lane per step: 1 measured fastest (13.0 against 13.6 ms for 4 and
-    // 14.4 ms for 8 on a 3.9e9-edge emit): the warps, not the lanes, keep the loads in flight
-    constexpr int U = 1;
-    for (int base = 0; base < total; base += 32 * U) {
-      long long dst[U];
-      unsigned src_u[U];
-      unsigned val[U];
-      bool ok[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        int e = base + 32 * q + lane;
-        // smallest lane l with incl_l > e (it has cnt_l > 0)
-        int lo = 0, hi = 31;
-#pragma unroll
-        for (int it = 0; it < 5; ++it) {
-          int mid = (lo + hi) >> 1;
-          int iv = __shfl_sync(FULL_MASK, incl, mid);
-          if (iv > e)
-            hi = mid;
-          else
-            lo = mid + 1;
+    const long long c0 = ib + (long long)c * chunk;
+    if (c0 >= ie) break;
+    const long long c1 = c0 + chunk < ie ? c0 + chunk : ie;
+    // position of the claim's first item (one graph search per claim); a warp cursor
+    // walks the claim 32 items at a time
+    int g0 = P.G == 1 ? 0 : graph_of_item(P.graphs, P.G, c0);
+    ItemPos p0 = item_pos(P.graphs[g0], c0 - P.graphs[g0].item_begin);
+    for (long long i0 = c0; i0 < c1; i0 += 32) {
+      if (i0 > c0) cursor_advance(P.graphs, g0, p0, 32);
+      const long long i = i0 + lane;
+      long long o = 0, pos = 0;
+      int cnt = 0;
+      unsigned uu = 0;
+      if (i < c1) {
+        o = offsets[i] - off_base;
+        long long cc = offsets[i + 1] - offsets[i];
+        pos = P.slot_base[i] - P.pool_shift;
+        if (cc <= (long long)slot_size(P, i)) cnt = (int)cc;  // else: not staged, regenerated
+        if (cnt > 0 && (pos < 0 || (unsigned long long)(pos + cnt) > P.pool_entries)) {  // checked, reported
+          set_error(P.err, CL_ERR_DEVICE);
+          cnt = 0;
         }
-        int il = __shfl_sync(FULL_MASK, incl, lo);
-        int cl = __shfl_sync(FULL_MASK, cnt, lo);
-        long long ol = __shfl_sync(FULL_MASK, o, lo);
-        long long pl = __shfl_sync(FULL_MASK, pos, lo);
-        src_u[q] = __shfl_sync(FULL_MASK, uu, lo);
-        ok[q] = e < total;
-        int local = e - (il - cl);
-        dst[q] = ol + local;
-        val[q] = ok[q] ? P.pool[pl + local] : 0u;
+        if (cnt > 0) {
+          int gi = g0;
+          ItemPos ip = p0;
+          cursor_advance(P.graphs, gi, ip, lane);
+          uu = ip.u;
+        }
       }
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        if (ok[q]) {
-          E pr;
-          pr.x = src_u[q];
-          pr.y = val[q];
-          edges[dst[q]] = pr;
+      // items with at least 32 staged edges: the whole warp copies one item at a
+      // time (lane = edge, coalesced, four loads in flight per lane)
+      unsigned big = __ballot_sync(FULL_MASK, cnt >= 32);
+      while (big) {
+        const int l = __ffs(big) - 1;
+        big &= big - 1;
+        const int cl = __shfl_sync(FULL_MASK, cnt, l);
+        const long long ol = __shfl_sync(FULL_MASK, o, l);
+        const long long pl = __shfl_sync(FULL_MASK, pos, l);
+        const unsigned su = __shfl_sync(FULL_MASK, uu, l);
+        for (int e0 = lane; e0 < cl; e0 += 32 * 4) {
+          unsigned v[4];
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = e0 + 32 * q < cl ? P.pool[pl + e0 + 32 * q] : 0u;
+  #pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (e0 + 32 * q < cl) {
+              E pr;
+              pr.x = su;
+              pr.y = v[q];
+              edges[ol + e0 + 32 * q] = pr;
+            }
+        }
+      }
+      if (cnt >= 32) cnt = 0;  // done above; the rest are flattened edge by edge
+      int incl = cnt;
+  #pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        int y = __shfl_up_sync(FULL_MASK, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const int total = __shfl_sync(FULL_MASK, incl, 31);
+      // edges per lane per step: 1 measured fastest (13.0 against 13.6 ms for 4 and
+      // 14.4 ms for 8 on a 3.9e9-edge emit): the warps, not the lanes, keep the loads in flight
+      constexpr int U = 1;
+      for (int base = 0; base < total; base += 32 * U) {
+        long long dst[U];
+        unsigned src_u[U];
+        unsigned val[U];
+        bool ok[U];
+  #pragma unroll
+        for (int q = 0; q < U; ++q) {
+          int e = base + 32 * q + lane;
+          // smallest lane l with incl_l > e (it has cnt_l > 0)
+          int lo = 0, hi = 31;
+  #pragma unroll
+          for (int it = 0; it < 5; ++it) {
+            int mid = (lo + hi) >> 1;
+            int iv = __shfl_sync(FULL_MASK, incl, mid);
+            if (iv > e)
+              hi = mid;
+            else
+              lo = mid + 1;
+          }
+          int il = __shfl_sync(FULL_MASK, incl, lo);
+          int cl = __shfl_sync(FULL_MASK, cnt, lo);
+          long long ol = __shfl_sync(FULL_MASK, o, lo);
+          long long pl = __shfl_sync(FULL_MASK, pos, lo);
+          src_u[q] = __shfl_sync(FULL_MASK, uu, lo);
+          ok[q] = e < total;
+          int local = e - (il - cl);
+          dst[q] = ol + local;
+          val[q] = ok[q] ? P.pool[pl + local] : 0u;
+        }
+  #pragma unroll
+        for (int q = 0; q < U; ++q) {
+          if (ok[q]) {
+            E pr;
+            pr.x = src_u[q];
+            pr.y = val[q];
+            edges[dst[q]] = pr;
+          }
         }
       }
     }
@@ -742,8 +751,9 @@ void launch_emit(const DevPlan& P, const DevGraph* single, const long long* d_of
                  cudaStream_t s) {
   cudaMemsetAsync(P.task_ctr, 0, sizeof(unsigned), s);
   if (staged) {
-    long long chunks = (r.ie - r.ib + 31) / 32;
-    long long cg = (chunks + 7) / 8;
+    // warps deal the output's COPY_EDGES-edge chunks round-robin; the item count bounds
+    // the useful grid from above (a chunk holds at least one item)
+    long long cg = (r.ie - r.ib + 8 * 32 - 1) / (8 * 32);
     int cgrid = (int)(cg < 4096 ? (cg < 1 ? 1 : cg) : 4096);
     if (copy_grid > 0 && cgrid > copy_grid) cgrid = copy_grid;
     if (etype == CL_E_I32)

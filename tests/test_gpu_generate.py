@@ -137,3 +137,10 @@ def test_generate_capacity_error_and_reuse():
     assert g.generate_into(full) == m
     assert np.array_equal(full.cpu().numpy().astype(np.int64), oracle_edges(w, 2))
     g.close()
+
+
+@pytest.mark.parametrize("tun,etype", [({}, 0), ({"stage_factor": -1.0}, 0), ({"tasks": 3}, 1)])
+def test_generate_small_degrees_wide_copy_claims(tun, etype):
+    """Items of about one edge each: the copy kernel takes 256 items per claim."""
+    w = inputs.powerlaw_degrees(300000, 2.9, 1, 40, 61)
+    assert np.array_equal(one_call(w, 4, etype=etype, **tun), oracle_edges(w, 4))
