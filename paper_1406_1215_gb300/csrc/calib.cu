@@ -9,9 +9,12 @@
 // The gradient of L = sum_u gE_u E_u (S depends on w):
 //   dL/dw_k = [gE_k A_k + B_k - K] / S,  B_k = G_{t_k} - [k >= t_k] gE_k w_k,
 //   G_j = sum_{u >= j} gE_u w_u,  K = sum_u gE_u (w_u / S) A_u.
-// Suffix sums and reductions are carried in double-double; the per-node terms
-// are rounded once to double.  FP64 is slow on this GPU (1/75 of FP32), but
-// these kernels make O(n log n) FP64 operations over a few arrays.
+// Suffix sums and reductions are carried in double-double (Dekker's sum); the
+// per-node terms are rounded once to double.  FP64 is slow on this GPU (1/75 of
+// FP32) and sets these kernels' time, so they spend as few FP64 operations as
+// they can: division by S is a product with a double-double 1/S formed once per
+// call, and t_u is found by a galloping search that ends at once for the nodes
+// with no capped partner (almost all of them).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -39,7 +42,7 @@ __device__ __forceinline__ dd dd_block_reduce(dd v) {
   __shared__ double rh[32], rl[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = dd_add(v, dd_shfl_xor(v, o));
+  for (int o = 16; o > 0; o >>= 1) v = dd_add_dekker(v, dd_shfl_xor(v, o));
   if (lane == 0) {
     rh[wid] = v.hi;
     rl[wid] = v.lo;
@@ -49,7 +52,7 @@ __device__ __forceinline__ dd dd_block_reduce(dd v) {
   if (wid == 0) {
     if (lane < nw) t = dd{rh[lane], rl[lane]};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t = dd_add(t, dd_shfl_xor(t, o));
+    for (int o = 16; o > 0; o >>= 1) t = dd_add_dekker(t, dd_shfl_xor(t, o));
   }
   __syncthreads();
   return t;  // valid in warp 0
@@ -64,7 +67,7 @@ __device__ __forceinline__ dd dd_block_excl(dd v, dd* tot) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     dd y = dd_shfl_up(inc, o);
-    if (lane >= o) inc = dd_add(inc, y);
+    if (lane >= o) inc = dd_add_dekker(inc, y);
   }
   if (lane == 31) {
     sh[wid] = inc.hi;
@@ -77,9 +80,9 @@ __device__ __forceinline__ dd dd_block_excl(dd v, dd* tot) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       dd y = dd_shfl_up(ti, o);
-      if (lane >= o) ti = dd_add(ti, y);
+      if (lane >= o) ti = dd_add_dekker(ti, y);
     }
-    dd ex = dd_add(ti, dd{-t.hi, -t.lo});
+    dd ex = dd_add_dekker(ti, dd{-t.hi, -t.lo});
     if (lane < nw) {
       sh[lane] = ex.hi;
       sl[lane] = ex.lo;
@@ -90,7 +93,7 @@ __device__ __forceinline__ dd dd_block_excl(dd v, dd* tot) {
     }
   }
   __syncthreads();
-  dd res = dd_add(dd{sh[wid], sl[wid]}, dd_add(inc, dd{-v.hi, -v.lo}));
+  dd res = dd_add_dekker(dd{sh[wid], sl[wid]}, dd_add_dekker(inc, dd{-v.hi, -v.lo}));
   *tot = dd{th, tl};
   __syncthreads();
   return res;
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(CT) suffix_reduce_kernel(const double* __restr
   dd acc{0.0, 0.0};
   for (int k = 0; k < CI; ++k) {
     long long j = j0 + (long long)k * CT + threadIdx.x;
-    if (j < n) acc = dd_add(acc, term(a, b, n - 1 - j));
+    if (j < n) acc = dd_add_dekker(acc, term(a, b, n - 1 - j));
   }
   dd t = dd_block_reduce(acc);
   if (threadIdx.x == 0) {
@@ -127,14 +130,14 @@ __global__ void suffix_partials_kernel(double* __restrict__ part, long long nt) 
     dd v = i < nt ? dd{part[2 * i], part[2 * i + 1]} : dd{0.0, 0.0};
     dd carry{ch, cl_};
     dd tot;
-    dd ex = dd_add(dd_block_excl(v, &tot), carry);
+    dd ex = dd_add_dekker(dd_block_excl(v, &tot), carry);
     if (i < nt) {
       part[2 * i] = ex.hi;
       part[2 * i + 1] = ex.lo;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      dd c = dd_add(carry, tot);
+      dd c = dd_add_dekker(carry, tot);
       ch = c.hi;
       cl_ = c.lo;
     }
@@ -151,13 +154,13 @@ __global__ void __launch_bounds__(CT) suffix_scan_kernel(const double* __restric
 #pragma unroll
   for (int k = 0; k < CI; ++k) {
     v[k] = (j0 + k < n) ? term(a, b, n - 1 - (j0 + k)) : dd{0.0, 0.0};
-    loc = dd_add(loc, v[k]);
+    loc = dd_add_dekker(loc, v[k]);
   }
   dd tot;
-  dd run = dd_add(dd_block_excl(loc, &tot), dd{part[2 * blockIdx.x], part[2 * blockIdx.x + 1]});
+  dd run = dd_add_dekker(dd_block_excl(loc, &tot), dd{part[2 * blockIdx.x], part[2 * blockIdx.x + 1]});
 #pragma unroll
   for (int k = 0; k < CI; ++k) {
-    run = dd_add(run, v[k]);  // inclusive prefix over reversed index = sum_{i >= n-1-j}
+    run = dd_add_dekker(run, v[k]);  // inclusive prefix over reversed index = sum_{i >= n-1-j}
     long long j = j0 + k;
     if (j < n) {
       long long i = n - 1 - j;
@@ -183,8 +186,13 @@ void suffix_sums(const double* a, const double* b, long long n, double* part, do
 }
 
 // t_u = #{v : fl(w_u w_v) >= S}: the capped partners form a prefix of the sorted w.
+// Galloping from v = 0 (w_0 is the largest weight, so fl(w_u w_0) < S means no
+// capped partner), then bisection: about 2 log2(t_u) products.
 __device__ __forceinline__ long long cap_threshold(const double* w, long long n, double wu, double S) {
-  long long lo = 0, hi = n;
+  if (!(wu * w[0] >= S)) return 0;
+  long long k = 1;  // w[k / 2] is a capped partner
+  while (k < n && wu * w[k] >= S) k *= 2;
+  long long lo = k / 2 + 1, hi = k < n ? k : n;  // the first non-partner lies in [lo, hi]
   while (lo < hi) {
     long long mid = (lo + hi) >> 1;
     if (wu * w[mid] >= S)
@@ -196,7 +204,7 @@ __device__ __forceinline__ long long cap_threshold(const double* w, long long n,
 }
 
 // forward: E_u, and per node t_u and A_u / S (the uncapped part's derivative dE_u/dw_u at fixed S)
-__global__ void __launch_bounds__(CT) expdeg_kernel(const double* __restrict__ w, long long n, double S,
+__global__ void __launch_bounds__(CT) expdeg_kernel(const double* __restrict__ w, long long n, double S, dd iS,
                                                     const double* __restrict__ R, double* __restrict__ E,
                                                     long long* __restrict__ tcap, double* __restrict__ Ahi,
                                                     double* __restrict__ Alo) {
@@ -205,10 +213,10 @@ __global__ void __launch_bounds__(CT) expdeg_kernel(const double* __restrict__ w
   double wu = w[u];
   long long t = cap_threshold(w, n, wu, S);
   dd A{R[2 * t], R[2 * t + 1]};
-  if (u >= t) A = dd_add(A, dd{-wu, 0.0});
-  dd part = dd_div(dd_mul_d(A, wu), dd{S, 0.0});  // (w_u / S) A_u
+  if (u >= t) A = dd_add_dekker(A, dd{-wu, 0.0});
+  dd part = dd_mul(dd_mul_d(A, wu), iS);  // (w_u / S) A_u
   double capped = (double)(t - (u < t ? 1 : 0));
-  dd e = dd_add(part, dd{capped, 0.0});
+  dd e = dd_add_dekker(part, dd{capped, 0.0});
   if (E) E[u] = e.hi + e.lo;
   if (tcap) tcap[u] = t;
   if (Ahi) {
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(CT) adj_K_kernel(const double* __restrict__ w,
     long long u = i0 + (long long)k * CT + threadIdx.x;
     if (u < n) {
       dd A{Ahi[u], Alo[u]};
-      acc = dd_add(acc, dd_mul_d(dd_mul_d(A, w[u]), gE[u]));
+      acc = dd_add_dekker(acc, dd_mul_d(dd_mul_d(A, w[u]), gE[u]));
     }
   }
   dd t = dd_block_reduce(acc);
@@ -237,19 +245,19 @@ __global__ void __launch_bounds__(CT) adj_K_kernel(const double* __restrict__ w,
   }
 }
 
-__global__ void sum_partials_kernel(const double* __restrict__ part, long long nt, double S, double* __restrict__ out) {
+__global__ void sum_partials_kernel(const double* __restrict__ part, long long nt, dd iS, double* __restrict__ out) {
   dd acc{0.0, 0.0};
-  for (long long i = threadIdx.x; i < nt; i += blockDim.x) acc = dd_add(acc, dd{part[2 * i], part[2 * i + 1]});
+  for (long long i = threadIdx.x; i < nt; i += blockDim.x) acc = dd_add_dekker(acc, dd{part[2 * i], part[2 * i + 1]});
   dd t = dd_block_reduce(acc);
   if (threadIdx.x == 0) {
-    dd K = dd_div(t, dd{S, 0.0});
+    dd K = dd_mul(t, iS);
     out[0] = K.hi;
     out[1] = K.lo;
   }
 }
 
 __global__ void __launch_bounds__(CT) adj_grad_kernel(const double* __restrict__ w, const double* __restrict__ gE,
-                                                      long long n, double S, const long long* __restrict__ tcap,
+                                                      long long n, dd iS, const long long* __restrict__ tcap,
                                                       const double* __restrict__ Ahi, const double* __restrict__ Alo,
                                                       const double* __restrict__ G, const double* __restrict__ Kp,
                                                       double* __restrict__ gw) {
@@ -260,10 +268,10 @@ __global__ void __launch_bounds__(CT) adj_grad_kernel(const double* __restrict__
   dd B{G[2 * t], G[2 * t + 1]};
   if (k >= t) {
     dd gw_k = dd_two_prod(gE[k], w[k]);
-    B = dd_add(B, dd{-gw_k.hi, -gw_k.lo});
+    B = dd_add_dekker(B, dd{-gw_k.hi, -gw_k.lo});
   }
-  dd num = dd_add(dd_add(dd_mul_d(A, gE[k]), B), dd{-Kp[0], -Kp[1]});
-  dd r = dd_div(num, dd{S, 0.0});
+  dd num = dd_add_dekker(dd_add_dekker(dd_mul_d(A, gE[k]), B), dd{-Kp[0], -Kp[1]});
+  dd r = dd_mul(num, iS);
   gw[k] = r.hi + r.lo;
 }
 
@@ -274,7 +282,7 @@ __global__ void __launch_bounds__(CT) sum_reduce_kernel(const double* __restrict
   dd acc{0.0, 0.0};
   for (int k = 0; k < CI; ++k) {
     long long i = i0 + (long long)k * CT + threadIdx.x;
-    if (i < n) acc = dd_add(acc, dd{w[i], 0.0});
+    if (i < n) acc = dd_add_dekker(acc, dd{w[i], 0.0});
   }
   dd t = dd_block_reduce(acc);
   if (threadIdx.x == 0) {
@@ -285,7 +293,7 @@ __global__ void __launch_bounds__(CT) sum_reduce_kernel(const double* __restrict
 
 __global__ void sum_final_kernel(const double* __restrict__ part, long long nt, double* __restrict__ out) {
   dd acc{0.0, 0.0};
-  for (long long i = threadIdx.x; i < nt; i += blockDim.x) acc = dd_add(acc, dd{part[2 * i], part[2 * i + 1]});
+  for (long long i = threadIdx.x; i < nt; i += blockDim.x) acc = dd_add_dekker(acc, dd{part[2 * i], part[2 * i + 1]});
   dd t = dd_block_reduce(acc);
   if (threadIdx.x == 0) out[0] = t.hi + t.lo;
 }
@@ -298,9 +306,9 @@ __global__ void __launch_bounds__(CT) relerr_kernel(const double* __restrict__ E
   long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double r = 0.0;
   if (u < n) {
-    double diff = E[u] - d[u];
-    r = fabs(diff) / d[u];
-    gE[u] = 2.0 * diff / d[u];  // dL/dE for L = sum (E - d)^2 / d
+    const double diff = E[u] - d[u], id = 1.0 / d[u];
+    r = fabs(diff) * id;
+    gE[u] = 2.0 * diff * id;  // dL/dE for L = sum (E - d)^2 / d
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(FULL_MASK, r, o));
@@ -309,10 +317,10 @@ __global__ void __launch_bounds__(CT) relerr_kernel(const double* __restrict__ E
 
 __global__ void __launch_bounds__(CT) step_kernel(double* __restrict__ w, const double* __restrict__ d,
                                                   const double* __restrict__ g, const double* __restrict__ Ahi,
-                                                  long long n, double S) {
+                                                  long long n, double iS) {
   long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (u >= n) return;
-  double J = Ahi[u] / S;
+  double J = Ahi[u] * iS;
   J = J > 1e-300 ? J : 1e-300;
   double H = 2.0 * J * J / d[u];
   double wn = w[u] - g[u] / H;
@@ -341,13 +349,29 @@ __global__ void __launch_bounds__(CT) runmin_tile_kernel(const double* __restric
   }
 }
 
+// exclusive running minimum of the tile minima (one block, 1024 values per round)
 __global__ void runmin_partials_kernel(double* __restrict__ part, long long nt) {
-  if (threadIdx.x != 0) return;
-  double m = INFINITY;
-  for (long long i = 0; i < nt; ++i) {  // exclusive running minimum of the tile minima
-    double v = part[i];
-    part[i] = m;
-    m = fmin(m, v);
+  __shared__ double sm[1024];
+  __shared__ double carry;
+  if (threadIdx.x == 0) carry = INFINITY;
+  __syncthreads();
+  for (long long base = 0; base < nt; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    const double v = i < nt ? part[i] : INFINITY;
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+      const double y = threadIdx.x >= (unsigned)o ? sm[threadIdx.x - o] : INFINITY;
+      __syncthreads();
+      sm[threadIdx.x] = fmin(sm[threadIdx.x], y);
+      __syncthreads();
+    }
+    const double c = carry;
+    const double ex = fmin(c, threadIdx.x > 0 ? sm[threadIdx.x - 1] : INFINITY);
+    __syncthreads();
+    if (i < nt) part[i] = ex;
+    if (threadIdx.x == blockDim.x - 1) carry = fmin(c, sm[threadIdx.x]);
+    __syncthreads();
   }
 }
 
@@ -431,17 +455,23 @@ void device_sum(const double* w, long long n, double* part, double* out, cudaStr
 
 unsigned nblk(long long n) { return (unsigned)((n + CT - 1) / CT); }
 
+// 1/S as a double-double: the rounded reciprocal and the rounded quotient of its exact residual
+dd inv_dd(double S) {
+  const double h = 1.0 / S;
+  return dd{h, std::fma(-h, S, 1.0) / S};
+}
+
 void forward(const double* w, long long n, double S, double* E, const CalWs& L, cudaStream_t s) {
   suffix_sums(w, nullptr, n, L.part, L.R, s);
-  expdeg_kernel<<<nblk(n), CT, 0, s>>>(w, n, S, L.R, E, L.t, L.Ahi, L.Alo);
+  expdeg_kernel<<<nblk(n), CT, 0, s>>>(w, n, S, inv_dd(S), L.R, E, L.t, L.Ahi, L.Alo);
 }
 
 void adjoint(const double* w, const double* gE, long long n, double S, double* gw, const CalWs& L, cudaStream_t s) {
   long long nt = (n + CTILE - 1) / CTILE;
   suffix_sums(gE, w, n, L.part, L.G, s);
   adj_K_kernel<<<(unsigned)nt, CT, 0, s>>>(w, gE, n, S, L.Ahi, L.Alo, L.part);
-  sum_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt, S, L.scal + 2);
-  adj_grad_kernel<<<nblk(n), CT, 0, s>>>(w, gE, n, S, L.t, L.Ahi, L.Alo, L.G, L.scal + 2, gw);
+  sum_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt, inv_dd(S), L.scal + 2);
+  adj_grad_kernel<<<nblk(n), CT, 0, s>>>(w, gE, n, inv_dd(S), L.t, L.Ahi, L.Alo, L.G, L.scal + 2, gw);
 }
 
 }  // namespace
@@ -496,7 +526,7 @@ extern "C" cl_status cl_expected_degree_adjoint(const double* d_w, const double*
   if (st != CL_OK) return st;
   // the forward quantities (R, t, A) the adjoint needs
   suffix_sums(d_w, nullptr, n, L.part, L.R, s);
-  expdeg_kernel<<<nblk(n), CT, 0, s>>>(d_w, n, S, L.R, nullptr, L.t, L.Ahi, L.Alo);
+  expdeg_kernel<<<nblk(n), CT, 0, s>>>(d_w, n, S, inv_dd(S), L.R, nullptr, L.t, L.Ahi, L.Alo);
   adjoint(d_w, d_gE, n, S, d_gw, L, s);
   return ok_last();
 }
@@ -531,9 +561,9 @@ extern "C" cl_status cl_calibrate(const double* d_target, int64_t n, double* d_w
     std::memcpy(&maxrel, &bits, sizeof(double));
     if (maxrel <= tol || it >= max_iter) break;
     adjoint(d_w, L.gE, n, S, L.g, L, s);
-    step_kernel<<<nblk(n), CT, 0, s>>>(d_w, d_target, L.g, L.Ahi, n, S);
+    step_kernel<<<nblk(n), CT, 0, s>>>(d_w, d_target, L.g, L.Ahi, n, 1.0 / S);
     runmin_tile_kernel<<<(unsigned)nt, CT, 0, s>>>(d_w, n, L.part);
-    runmin_partials_kernel<<<1, 32, 0, s>>>(L.part, nt);
+    runmin_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt);
     runmin_apply_kernel<<<(unsigned)nt, CT, 0, s>>>(d_w, n, L.part);
     if (ok_last() != CL_OK) return CL_ERR_CUDA;
   }
