@@ -146,6 +146,60 @@ __device__ __forceinline__ bool accept_ratio(unsigned long long k, unsigned w_pr
   return L < ((unsigned long long)w_t << 21);
 }
 
+// A capped run at an item's first position `target` (p = 1 there): the weights are
+// sorted, so every position from target up to the first v with Q(v) < S (or the
+// item's end) has p = 1, and Algorithm 1 takes each of them as an edge (skip 0,
+// acceptance certain), one draw per position.  The run's end is found by bisection
+// over the weights and its edges are written in one go (staged in whole sectors, or
+// emitted) instead of one loop iteration per edge.  The draw that follows the run
+// (number L of the item's stream) is made here too.
+struct RunEnd {
+  unsigned L, z, w;
+  ff lr;
+};
+template <int MODE, bool WF, typename E>
+__device__ __forceinline__ RunEnd capped_run(const typename Wt<WF>::w_t* __restrict__ W, typename Wt<WF>::w_t wu,
+                                          typename Wt<WF>::q_t S, unsigned target, unsigned end, unsigned u,
+                                          unsigned seg, unsigned key0, unsigned key1, unsigned* pool,
+                                          unsigned long long sbase, unsigned ssize, int* overflow, unsigned* sg,
+                                          E* edges, long long capacity) {
+  using T = Wt<WF>;
+  unsigned lo = target + 1, hi = end;
+  while (lo < hi) {
+    const unsigned mid = lo + ((hi - lo) >> 1);
+    if (T::Q(wu, __ldg(&W[mid]), S) < S)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  const unsigned L = lo - target;
+  if (MODE == MODE_STAGE) {
+    const unsigned m = L < ssize ? L : ssize;  // the slot is a multiple of 8 entries
+    unsigned g = 0;
+    for (; g + GROUP <= m; g += GROUP) {
+      uint4* dst = (uint4*)(pool + sbase + g);
+      const unsigned v = target + g;
+      dst[0] = make_uint4(v, v + 1, v + 2, v + 3);
+      dst[1] = make_uint4(v + 4, v + 5, v + 6, v + 7);
+    }
+    for (unsigned e = 0; g + e < m; ++e) sg[e * SAMPLER_THREADS] = target + g + e;  // the open group
+    if (L > ssize) atomicExch(overflow, 1);  // the item outgrew its slot: EMIT regenerates it
+  }
+  if (MODE == MODE_EMIT) {
+    for (unsigned i = 0; i < L; ++i) {
+      const long long pos = (long long)sbase + i;
+      if (pos < capacity) {
+        E e;
+        e.x = u;
+        e.y = target + i;
+        edges[pos] = e;
+      }
+    }
+  }
+  const u32x4 nb = philox4x32_10(u32x4{L, seg, u, 0u}, key0, key1);
+  return RunEnd{L, nb.z, nb.w, ff_neglog_r53_w(nb.x, nb.y)};
+}
+
 // A warp's queue of up to 32 upcoming items with their set-up data, and the
 // feed it is filled from (shared memory; see sample_kernel).
 template <typename w_t>
@@ -542,7 +596,22 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
         else if (Qt < S)
           Lp = T::Lp(Qt, S, SINGLE ? G1 : P.graphs[gi_l]);
       }
-      j = fresh ? target : target + 1;
+      if (fresh && Qt == S && Qt != 0) {  // a capped run from the first position (S = 0: no edge)
+        unsigned* sg = nullptr;
+        if (MODE == MODE_STAGE) sg = &sgrp[0][threadIdx.x];
+        const unsigned key0 = SINGLE ? G1.key0 : P.graphs[gi_l].key0, key1 = SINGLE ? G1.key1 : P.graphs[gi_l].key1;
+        const RunEnd r = capped_run<MODE, WF, E>(W, wu, S, target, end, u, seg, key0, key1, P.pool, sbase, ssize,
+                                                 P.overflow, sg, edges, capacity);
+        k = r.L;  // its positions' draws are consumed: the next draw is number L
+        t = r.L;
+        n_iter += r.L;
+        j = target + r.L;
+        pz = r.z;
+        pw = r.w;
+        pLr = r.lr;
+      } else {
+        j = fresh ? target : target + 1;
+      }
       if (j >= end) ended = true;
       fresh = false;
     }
