@@ -288,3 +288,22 @@ def test_table1_er_network():
         if Eh is None:
             Eh = E.cpu().numpy().astype(np.int64)
         assert np.array_equal(Eh[int(off[a]):int(off[a + 20])], og.generate(a, a + 20)), a
+
+
+@pytest.mark.parametrize("tun,etype", [({}, 0), ({}, 1), ({"stage_factor": -1.0}, 0), ({"no_stage": 1}, 1),
+                                       ({"tasks": 2}, 0)])
+def test_parity_long_capped_runs(tun, etype):
+    """Five hub rows whose every partner is capped (w_u w_v >= S for all v): their
+    capped runs span two 2^16-wide segments and are written in one go; with 8-entry
+    slots (stage_factor -1) they outgrow the slot and the emit pass regenerates them,
+    and without staging the emit pass writes the runs itself.  Edges, counts and the
+    loop-iteration total equal the oracle's (one draw per capped position)."""
+    w = np.concatenate([np.full(5, 300000), np.full(100000, 10), np.full(3000, 1)]).astype(np.int32)
+    Eg, cg, st = gpu_generate(w, 17, etype=etype, **tun)
+    stats = oracle.Stats()
+    Eo, co, g = oracle_generate(w, 17)
+    oracle.Graph(w, 17).count_items(stats=stats)
+    assert np.array_equal(cg, co)
+    assert np.array_equal(Eg, Eo)
+    assert st["iterations"] == stats.iterations
+    assert int(co[0]) == 65535  # the first hub's first segment is one capped run
