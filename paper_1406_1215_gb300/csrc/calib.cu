@@ -9,8 +9,9 @@
 // The gradient of L = sum_u gE_u E_u (S depends on w):
 //   dL/dw_k = [gE_k A_k + B_k - K] / S,  B_k = G_{t_k} - [k >= t_k] gE_k w_k,
 //   G_j = sum_{u >= j} gE_u w_u,  K = sum_u gE_u (w_u / S) A_u.
-// Suffix sums and reductions are carried in double-double (Dekker's sum); the
-// per-node terms are rounded once to double.  FP64 is slow on this GPU (1/75 of
+// Sums are carried in double-double (Dekker's sum); the per-node terms are
+// rounded once to double.  R and G are needed only at the thresholds t_u <= t_0,
+// so they come from one reduction over all nodes and a prefix over the first t_0.  FP64 is slow on this GPU (1/75 of
 // FP32) and sets these kernels' time, so they spend as few FP64 operations as
 // they can: division by S is a product with a double-double 1/S formed once per
 // call, and t_u is found by a galloping search that ends at once for the nodes
@@ -99,28 +100,12 @@ __device__ __forceinline__ dd dd_block_excl(dd v, dd* tot) {
   return res;
 }
 
-// x_i of a suffix sum: w_i, or the exact product gE_i w_i
+// x_i of a tail sum: w_i, or the exact product gE_i w_i
 __device__ __forceinline__ dd term(const double* a, const double* b, long long i) {
   return b ? dd_two_prod(a[i], b[i]) : dd{a[i], 0.0};
 }
 
-// Suffix sums R[k] = sum_{i >= k} x_i, k = 0..n (R[n] = 0), computed on the
-// reversed index j = n-1-i as an inclusive prefix: tile sums, their scan, tile scan.
-__global__ void __launch_bounds__(CT) suffix_reduce_kernel(const double* __restrict__ a, const double* __restrict__ b,
-                                                           long long n, double* __restrict__ part) {
-  long long j0 = blockIdx.x * (long long)CTILE;
-  dd acc{0.0, 0.0};
-  for (int k = 0; k < CI; ++k) {
-    long long j = j0 + (long long)k * CT + threadIdx.x;
-    if (j < n) acc = dd_add_dekker(acc, term(a, b, n - 1 - j));
-  }
-  dd t = dd_block_reduce(acc);
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = t.hi;
-    part[2 * blockIdx.x + 1] = t.lo;
-  }
-}
-
+// Exclusive scan, in place, of nt double-double tile sums (one block, 1024 at a time).
 __global__ void suffix_partials_kernel(double* __restrict__ part, long long nt) {
   __shared__ double ch, cl_;
   if (threadIdx.x == 0) ch = cl_ = 0.0;
@@ -145,44 +130,71 @@ __global__ void suffix_partials_kernel(double* __restrict__ part, long long nt) 
   }
 }
 
-__global__ void __launch_bounds__(CT) suffix_scan_kernel(const double* __restrict__ a, const double* __restrict__ b,
-                                                         long long n, const double* __restrict__ part,
-                                                         double* __restrict__ R) {
-  long long j0 = blockIdx.x * (long long)CTILE + (long long)threadIdx.x * CI;
+// Tail sums X_k = sum_{i >= k} x_i are needed only at the thresholds t_u, and
+// t_u <= t_0 for every u (w_0 is the largest weight), so they are formed as
+// X_k = total - sum_{i < k} x_i for k <= m = t_0 alone: one reduction over all n
+// values and a prefix over the first m, instead of a scan over all n.  The
+// subtraction is the accurate double-double sum (the two terms may nearly cancel).
+// Tile sums of x_i over [0, n), or over [0, min(*mp, n)) when mp is given (tiles
+// past it write zero).
+__global__ void __launch_bounds__(CT) tile_sum_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                      long long n, const long long* __restrict__ mp,
+                                                      double* __restrict__ part) {
+  const long long m = mp ? (*mp < n ? *mp : n) : n;
+  const long long i0 = blockIdx.x * (long long)CTILE;
+  dd acc{0.0, 0.0};
+  if (i0 < m) {
+    for (int k = 0; k < CI; ++k) {
+      const long long i = i0 + (long long)k * CT + threadIdx.x;
+      if (i < m) acc = dd_add_dekker(acc, term(a, b, i));
+    }
+  }
+  const dd t = dd_block_reduce(acc);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = t.hi;
+    part[2 * blockIdx.x + 1] = t.lo;
+  }
+}
+
+// The double-double total of nt tile sums (one block) into tot[0..1].
+__global__ void total_kernel(const double* __restrict__ part, long long nt, double* __restrict__ tot) {
+  dd acc{0.0, 0.0};
+  for (long long i = threadIdx.x; i < nt; i += blockDim.x) acc = dd_add_dekker(acc, dd{part[2 * i], part[2 * i + 1]});
+  const dd t = dd_block_reduce(acc);
+  if (threadIdx.x == 0) {
+    tot[0] = t.hi;
+    tot[1] = t.lo;
+  }
+}
+
+// X_k = tot - sum_{i < k} x_i for k = 0 .. m (part: the exclusive prefix of the tile sums).
+__global__ void __launch_bounds__(CT) tail_scan_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                       long long n, const long long* __restrict__ mp,
+                                                       const double* __restrict__ part, const double* __restrict__ tot,
+                                                       double* __restrict__ X) {
+  const long long m = *mp < n ? *mp : n;
+  if (blockIdx.x * (long long)CTILE > m) return;  // the whole block: no index <= m here
+  const long long k0 = blockIdx.x * (long long)CTILE + (long long)threadIdx.x * CI;
   dd v[CI];
   dd loc{0.0, 0.0};
 #pragma unroll
   for (int k = 0; k < CI; ++k) {
-    v[k] = (j0 + k < n) ? term(a, b, n - 1 - (j0 + k)) : dd{0.0, 0.0};
+    v[k] = (k0 + k < m) ? term(a, b, k0 + k) : dd{0.0, 0.0};
     loc = dd_add_dekker(loc, v[k]);
   }
-  dd tot;
-  dd run = dd_add_dekker(dd_block_excl(loc, &tot), dd{part[2 * blockIdx.x], part[2 * blockIdx.x + 1]});
+  dd t;
+  dd run = dd_add_dekker(dd_block_excl(loc, &t), dd{part[2 * blockIdx.x], part[2 * blockIdx.x + 1]});
+  const dd T{tot[0], tot[1]};
 #pragma unroll
   for (int k = 0; k < CI; ++k) {
-    run = dd_add_dekker(run, v[k]);  // inclusive prefix over reversed index = sum_{i >= n-1-j}
-    long long j = j0 + k;
-    if (j < n) {
-      long long i = n - 1 - j;
-      R[2 * i] = run.hi;
-      R[2 * i + 1] = run.lo;
+    const long long idx = k0 + k;
+    if (idx <= m) {
+      const dd x = idx == n ? dd{0.0, 0.0} : dd_add(T, dd{-run.hi, -run.lo});
+      X[2 * idx] = x.hi;
+      X[2 * idx + 1] = x.lo;
     }
+    run = dd_add_dekker(run, v[k]);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    R[2 * n] = 0.0;
-    R[2 * n + 1] = 0.0;
-  }
-}
-
-void suffix_sums(const double* a, const double* b, long long n, double* part, double* R, cudaStream_t s) {
-  long long nt = (n + CTILE - 1) / CTILE;
-  if (n <= 0) {
-    cudaMemsetAsync(R, 0, 2 * sizeof(double), s);
-    return;
-  }
-  suffix_reduce_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, part);
-  suffix_partials_kernel<<<1, 1024, 0, s>>>(part, nt);
-  suffix_scan_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, part, R);
 }
 
 // t_u = #{v : fl(w_u w_v) >= S}: the capped partners form a prefix of the sorted w.
@@ -201,6 +213,12 @@ __device__ __forceinline__ long long cap_threshold(const double* w, long long n,
       hi = mid;
   }
   return lo;
+}
+
+// m = t_0, the largest threshold (the heaviest node's)
+__global__ void t0_kernel(const double* __restrict__ w, long long n, const double* __restrict__ sc,
+                          long long* __restrict__ t0) {
+  *t0 = cap_threshold(w, n, w[0], sc[0]);
 }
 
 // forward: E_u, and per node t_u and A_u / S (the uncapped part's derivative dE_u/dw_u at fixed S)
@@ -412,7 +430,7 @@ __global__ void __launch_bounds__(CT) runmin_apply_kernel(double* __restrict__ w
 }
 
 // The call's S and its double-double reciprocal, sc = {S, 1/S hi, 1/S lo}: from a
-// given S, or from R_0 = sum w of the forward pass's suffix sums (rounded once).
+// given S, or from the forward pass's double-double sum of w (rounded once).
 __device__ __forceinline__ void put_scal(double S, double* sc) {
   const double h = 1.0 / S;
   sc[0] = S;
@@ -420,8 +438,8 @@ __device__ __forceinline__ void put_scal(double S, double* sc) {
   sc[2] = fma(-h, S, 1.0) / S;
 }
 __global__ void scal_set_kernel(double S, double* __restrict__ sc) { put_scal(S, sc); }
-__global__ void scal_from_R_kernel(const double* __restrict__ R, double* __restrict__ sc) {
-  put_scal(R[0] + R[1], sc);
+__global__ void scal_from_total_kernel(const double* __restrict__ tot, double* __restrict__ sc) {
+  put_scal(tot[0] + tot[1], sc);
 }
 
 struct CalWs {
@@ -431,7 +449,8 @@ struct CalWs {
   double* Ahi;    // n
   double* Alo;    // n
   double* part;   // 2 tiles
-  double* scal;   // 8: S, 1/S (2), -, K (2)
+  double* scal;   // 16: S, 1/S (2), -, K (2), sum w (2), sum gE w (2)
+  long long* t0;  // the largest threshold
   unsigned long long* maxbits;
   double* E;      // n (calibration)
   double* gE;     // n (calibration)
@@ -457,7 +476,8 @@ CalWs cal_layout(void* base, long long n, bool calib) {
   L.Ahi = (double*)take(sizeof(double) * (n > 0 ? n : 1));
   L.Alo = (double*)take(sizeof(double) * (n > 0 ? n : 1));
   L.part = (double*)take(sizeof(double) * 2 * nt);
-  L.scal = (double*)take(sizeof(double) * 8);
+  L.scal = (double*)take(sizeof(double) * 16);
+  L.t0 = (long long*)take(sizeof(long long) * 2);
   L.maxbits = (unsigned long long*)take(sizeof(unsigned long long) * 2);
   L.E = calib ? (double*)take(sizeof(double) * (n > 0 ? n : 1)) : nullptr;
   L.gE = calib ? (double*)take(sizeof(double) * (n > 0 ? n : 1)) : nullptr;
@@ -475,16 +495,34 @@ void device_sum(const double* w, long long n, double* part, double* out, cudaStr
 
 unsigned nblk(long long n) { return (unsigned)((n + CT - 1) / CT); }
 
-// E and the per-node forward quantities; S from L.scal, or (sum_S) taken there from R_0
+// X_k = sum_{i >= k} x_i for k <= t_0 (x_i = a_i, or a_i b_i exactly); tot: the total
+// m = t_0 must be in L.t0 (the forward pass puts it there)
+void tail_sums(const double* a, const double* b, long long n, const CalWs& L, double* tot, double* X, bool total,
+               cudaStream_t s) {
+  const long long nt = (n + CTILE - 1) / CTILE;
+  if (total) {
+    tile_sum_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, nullptr, L.part);
+    total_kernel<<<1, 1024, 0, s>>>(L.part, nt, tot);
+  }
+  tile_sum_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, L.t0, L.part);
+  suffix_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt);
+  tail_scan_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, L.t0, L.part, tot, X);
+}
+
+// E and the per-node forward quantities; S from L.scal, or (sum_S) the sum of w put there
 void forward(const double* w, long long n, bool sum_S, double* E, const CalWs& L, cudaStream_t s) {
-  suffix_sums(w, nullptr, n, L.part, L.R, s);
-  if (sum_S) scal_from_R_kernel<<<1, 1, 0, s>>>(L.R, L.scal);
+  const long long nt = (n + CTILE - 1) / CTILE;
+  tile_sum_kernel<<<(unsigned)nt, CT, 0, s>>>(w, nullptr, n, nullptr, L.part);
+  total_kernel<<<1, 1024, 0, s>>>(L.part, nt, L.scal + 6);
+  if (sum_S) scal_from_total_kernel<<<1, 1, 0, s>>>(L.scal + 6, L.scal);
+  t0_kernel<<<1, 1, 0, s>>>(w, n, L.scal, L.t0);
+  tail_sums(w, nullptr, n, L, L.scal + 6, L.R, false, s);
   expdeg_kernel<<<nblk(n), CT, 0, s>>>(w, n, L.scal, L.R, E, L.t, L.Ahi, L.Alo);
 }
 
 void adjoint(const double* w, const double* gE, long long n, double* gw, const CalWs& L, cudaStream_t s) {
   long long nt = (n + CTILE - 1) / CTILE;
-  suffix_sums(gE, w, n, L.part, L.G, s);
+  tail_sums(gE, w, n, L, L.scal + 8, L.G, true, s);
   adj_K_kernel<<<(unsigned)nt, CT, 0, s>>>(w, gE, n, L.Ahi, L.Alo, L.part);
   sum_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt, L.scal, L.scal + 4);
   adj_grad_kernel<<<nblk(n), CT, 0, s>>>(w, gE, n, L.scal, L.t, L.Ahi, L.Alo, L.G, L.scal + 4, gw);
@@ -562,7 +600,7 @@ extern "C" cl_status cl_calibrate(const double* d_target, int64_t n, double* d_w
   double S = 0, maxrel = INFINITY;
   int it = 0;
   for (;; ++it) {
-    // S = R_0 of the forward pass's suffix sums, kept on the device; one host read per
+    // S = the forward pass's sum of w, kept on the device; one host read per
     // iteration (the convergence test)
     cudaMemsetAsync(L.maxbits, 0, sizeof(unsigned long long), s);
     unsigned long long bits = 0;
