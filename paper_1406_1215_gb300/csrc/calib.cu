@@ -106,7 +106,11 @@ __device__ __forceinline__ dd term(const double* a, const double* b, long long i
 }
 
 // Exclusive scan, in place, of nt double-double tile sums (one block, 1024 at a time).
-__global__ void suffix_partials_kernel(double* __restrict__ part, long long nt) {
+__global__ void suffix_partials_kernel(double* __restrict__ part, long long nt, const long long* __restrict__ mp) {
+  if (mp) {  // only the tiles up to the one holding index m are read afterwards
+    const long long tm = *mp / CTILE + 1;
+    nt = tm < nt ? tm : nt;
+  }
   __shared__ double ch, cl_;
   if (threadIdx.x == 0) ch = cl_ = 0.0;
   __syncthreads();
@@ -247,22 +251,31 @@ __global__ void __launch_bounds__(CT) expdeg_kernel(const double* __restrict__ w
 }
 
 // K = sum_u gE_u (w_u / S) A_u (block partial sums, dd)
+// tile sums of gE_u w_u A_u (for K) and of gE_u w_u (the total of G), in one pass
 __global__ void __launch_bounds__(CT) adj_K_kernel(const double* __restrict__ w, const double* __restrict__ gE,
                                                    long long n, const double* __restrict__ Ahi,
-                                                   const double* __restrict__ Alo, double* __restrict__ part) {
+                                                   const double* __restrict__ Alo, double* __restrict__ part,
+                                                   double* __restrict__ partG) {
   long long i0 = blockIdx.x * (long long)CTILE;
-  dd acc{0.0, 0.0};
+  dd acc{0.0, 0.0}, accG{0.0, 0.0};
   for (int k = 0; k < CI; ++k) {
     long long u = i0 + (long long)k * CT + threadIdx.x;
     if (u < n) {
       dd A{Ahi[u], Alo[u]};
-      acc = dd_add_dekker(acc, dd_mul_d(dd_mul_d(A, w[u]), gE[u]));
+      const double wu = w[u], gu = gE[u];
+      acc = dd_add_dekker(acc, dd_mul_d(dd_mul_d(A, wu), gu));
+      accG = dd_add_dekker(accG, dd_two_prod(gu, wu));
     }
   }
   dd t = dd_block_reduce(acc);
   if (threadIdx.x == 0) {
     part[2 * blockIdx.x] = t.hi;
     part[2 * blockIdx.x + 1] = t.lo;
+  }
+  t = dd_block_reduce(accG);
+  if (threadIdx.x == 0) {
+    partG[2 * blockIdx.x] = t.hi;
+    partG[2 * blockIdx.x + 1] = t.lo;
   }
 }
 
@@ -449,6 +462,7 @@ struct CalWs {
   double* Ahi;    // n
   double* Alo;    // n
   double* part;   // 2 tiles
+  double* part2;  // 2 tiles
   double* scal;   // 16: S, 1/S (2), -, K (2), sum w (2), sum gE w (2)
   long long* t0;  // the largest threshold
   unsigned long long* maxbits;
@@ -476,6 +490,7 @@ CalWs cal_layout(void* base, long long n, bool calib) {
   L.Ahi = (double*)take(sizeof(double) * (n > 0 ? n : 1));
   L.Alo = (double*)take(sizeof(double) * (n > 0 ? n : 1));
   L.part = (double*)take(sizeof(double) * 2 * nt);
+  L.part2 = (double*)take(sizeof(double) * 2 * nt);
   L.scal = (double*)take(sizeof(double) * 16);
   L.t0 = (long long*)take(sizeof(long long) * 2);
   L.maxbits = (unsigned long long*)take(sizeof(unsigned long long) * 2);
@@ -495,17 +510,13 @@ void device_sum(const double* w, long long n, double* part, double* out, cudaStr
 
 unsigned nblk(long long n) { return (unsigned)((n + CT - 1) / CT); }
 
-// X_k = sum_{i >= k} x_i for k <= t_0 (x_i = a_i, or a_i b_i exactly); tot: the total
+// X_k = sum_{i >= k} x_i for k <= t_0 (x_i = a_i, or a_i b_i exactly), given tot = the total
 // m = t_0 must be in L.t0 (the forward pass puts it there)
-void tail_sums(const double* a, const double* b, long long n, const CalWs& L, double* tot, double* X, bool total,
+void tail_sums(const double* a, const double* b, long long n, const CalWs& L, const double* tot, double* X,
                cudaStream_t s) {
   const long long nt = (n + CTILE - 1) / CTILE;
-  if (total) {
-    tile_sum_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, nullptr, L.part);
-    total_kernel<<<1, 1024, 0, s>>>(L.part, nt, tot);
-  }
   tile_sum_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, L.t0, L.part);
-  suffix_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt);
+  suffix_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt, L.t0);
   tail_scan_kernel<<<(unsigned)nt, CT, 0, s>>>(a, b, n, L.t0, L.part, tot, X);
 }
 
@@ -516,15 +527,16 @@ void forward(const double* w, long long n, bool sum_S, double* E, const CalWs& L
   total_kernel<<<1, 1024, 0, s>>>(L.part, nt, L.scal + 6);
   if (sum_S) scal_from_total_kernel<<<1, 1, 0, s>>>(L.scal + 6, L.scal);
   t0_kernel<<<1, 1, 0, s>>>(w, n, L.scal, L.t0);
-  tail_sums(w, nullptr, n, L, L.scal + 6, L.R, false, s);
+  tail_sums(w, nullptr, n, L, L.scal + 6, L.R, s);
   expdeg_kernel<<<nblk(n), CT, 0, s>>>(w, n, L.scal, L.R, E, L.t, L.Ahi, L.Alo);
 }
 
 void adjoint(const double* w, const double* gE, long long n, double* gw, const CalWs& L, cudaStream_t s) {
   long long nt = (n + CTILE - 1) / CTILE;
-  tail_sums(gE, w, n, L, L.scal + 8, L.G, true, s);
-  adj_K_kernel<<<(unsigned)nt, CT, 0, s>>>(w, gE, n, L.Ahi, L.Alo, L.part);
+  adj_K_kernel<<<(unsigned)nt, CT, 0, s>>>(w, gE, n, L.Ahi, L.Alo, L.part, L.part2);
   sum_partials_kernel<<<1, 1024, 0, s>>>(L.part, nt, L.scal, L.scal + 4);
+  total_kernel<<<1, 1024, 0, s>>>(L.part2, nt, L.scal + 8);  // sum_u gE_u w_u
+  tail_sums(gE, w, n, L, L.scal + 8, L.G, s);
   adj_grad_kernel<<<nblk(n), CT, 0, s>>>(w, gE, n, L.scal, L.t, L.Ahi, L.Alo, L.G, L.scal + 4, gw);
 }
 
