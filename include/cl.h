@@ -377,7 +377,10 @@ void cl_plan_destroy(cl_plan* plan);
  * from different host threads -- race and corrupt each other's result:
  * serialise them.  Asynchronous on `stream`; d_counts and d_offsets are
  * caller-owned device arrays of n and n + 1 entries and must not overlap.
- * Errors: CL_ERR_INVALID_ARG, CL_ERR_RANGE, CL_ERR_CUDA. */
+ * Errors: CL_ERR_INVALID_ARG, CL_ERR_RANGE, CL_ERR_CUDA (as for every call of
+ * this library, the launch check reads and clears the calling thread's last
+ * CUDA error, so an error left pending by earlier, unrelated work is reported
+ * here too). */
 cl_status cl_scan_noalloc(const int32_t* d_counts, int64_t n, int64_t* d_offsets, cl_stream_t stream);
 
 /* --- diagnostics (exercise one primitive over arrays; for tests) ---------- */
