@@ -17,7 +17,9 @@
 //   Q_prev = Q_v (recompute L_p if it changed); j = v + 1
 // A new item's first position is handled by the same weight-lookup and
 // L_p stages as a candidate (Q_prev = Q(j0)), so set-up shares the code of
-// the loop body instead of running as a separate divergent branch.
+// the loop body instead of running as a separate divergent branch; when that
+// position is capped (p = 1), the whole capped run is taken at once
+// (capped_run: the same edges and draws as one iteration per position).
 //
 // Modes: COUNT writes per-item edge counts; STAGE also writes each item's
 // destinations, in order, into the item's slot of a staging pool (slot sizes
