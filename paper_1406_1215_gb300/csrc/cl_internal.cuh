@@ -297,19 +297,6 @@ __device__ __forceinline__ unsigned slot_size(const DevPlan& P, long long i) {
   return (unsigned long long)(b - P.pool_shift) <= P.pool_cap ? (unsigned)(b - P.slot_base[i]) : 0u;
 }
 
-// Weight of node v of a graph with weights W and uniform-block entries blk:
-// from the lane's cached run (v < run_end), else from the block table, else
-// (a block holding a change of weight) from W itself.
-__device__ __forceinline__ int block_weight(const unsigned long long* __restrict__ blk, const int* W, unsigned v,
-                                            unsigned& run_end, int& run_w) {
-  if (v < run_end) return run_w;
-  const unsigned long long e = __ldg(&blk[v >> BLK_SHIFT]);
-  if (e == BLK_MIXED) return __ldg(&W[v]);
-  run_w = (int)(unsigned)(e >> 32);
-  run_end = (unsigned)e;
-  return run_w;
-}
-
 // ---- launchers implemented in plan.cu / sample.cu / diag.cu ----
 constexpr int ANALYZE_CHUNK_HOST = 4096;  // weights per analysis block (matches plan.cu)
 constexpr int SCAN_TILE_HOST = 2048;      // elements per scan tile (matches plan.cu)

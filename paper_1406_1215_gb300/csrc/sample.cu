@@ -279,8 +279,6 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
   unsigned wprev = 0;        // integer weights: w of the last candidate (Q_prev = w_u w_prev unless capped)
   unsigned pz = 0, pw = 0;   // the lane's next draw (index t): acceptance words ...
   ff pLr{0.f, 0.f};          // ... and its -ln r_s
-  unsigned run_end = 0;      // integer weights: candidates before run_end weigh run_w
-  int run_w = 0;
   int gi_l = 0;              // graph of the lane's item (batched plans)
   const w_t* w_l = nullptr;
   q_t S_l = 0;
@@ -527,7 +525,6 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
           keys.k1 = g.key1;
         }
       }
-      run_end = 0;  // no cached run for the new item
       t = 0;
       k = 0;
       target = j0;  // first position: p = Q(j0) / S
@@ -540,9 +537,11 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
       w_t wt;
       if (WF) {
         wt = __ldg(&W[target]);
-      } else {  // integer weights: uniform-block table, the lane's current run as a cache
+      } else {  // integer weights: the uniform-block table (an L1/L2-resident read; no per-lane cache)
         const unsigned long long* blk = SINGLE ? G1.blkp : P.graphs[gi_l].blkp;
-        wt = (w_t)block_weight(blk, (const int*)W, target, run_end, run_w);
+        const unsigned long long be = __ldg(&blk[target >> BLK_SHIFT]);  // (w << 32) | run end, or mixed
+        wt = (w_t)(int)(unsigned)(be >> 32);
+        if (be == BLK_MIXED) wt = (w_t)__ldg(&((const int*)W)[target]);
       }
       const unsigned az = pz, aw = pw;  // acceptance words of the draw that made the candidate
       {
