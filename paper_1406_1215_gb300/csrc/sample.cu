@@ -552,13 +552,19 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
       }
       const q_t Qt = T::Q(wu, wt, S);
       // ---- (6) acceptance r_a < q / p, with the draw that made the candidate
-      if (!fresh) {
+      {
         bool acc;
-        if (!WF) {  // equal weights pass the ratio test ((2k+1) w < 2^53 w): no separate branch for them
+        if (!WF) {
+          // equal weights pass the ratio test ((2k+1) w < 2^53 w), so they need no branch of
+          // their own; the test is cheap enough to run for a new item's first position too and
+          // be masked, which keeps a branch on `fresh` out of the loop
           if (Qprev != S)
             acc = accept_ratio(grid52(az, aw), wprev, (unsigned)wt);
           else
             acc = T::accept(grid52(az, aw), Qprev, Qt);
+          acc = acc && !fresh;
+        } else if (fresh) {
+          acc = false;
         } else if (Qt == Qprev) {
           acc = true;
         } else {
