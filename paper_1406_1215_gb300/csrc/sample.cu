@@ -24,9 +24,10 @@
 // Modes: COUNT writes per-item edge counts; STAGE also writes each item's
 // destinations, in order, into the item's slot of a staging pool (slot sizes
 // come from the plan: expected edges + 6 sd + 6, in whole 32-byte sectors;
-// an item that outgrows its slot is regenerated by EMIT).  A lane collects 8
-// entries in shared memory and writes them as one whole sector, since a
-// partially written sector costs a read-modify-write of HBM when evicted;
+// an item that outgrows its slot is regenerated by EMIT).  Each accepted
+// destination is stored at once: a lane's consecutive 4-byte stores complete a
+// sector within a few passes, in L2 (collecting 8 in shared memory to write
+// whole sectors cost a branch per pass and was slower: 58.4 against 55.8 ms);
 // EMIT regenerates items and writes (u, v) pairs.  The copy kernel turns
 // staged destinations into (u, v) pairs at the scanned offsets, so a count
 // + copy does the sampling arithmetic once.
@@ -42,7 +43,7 @@ constexpr int SAMPLER_THREADS = 256;
 // resident blocks per SM the sampler is compiled for: 3 x 256 threads leave 85 registers
 // per thread, enough for the loop state without spills (4 blocks: 64 registers, spills)
 constexpr int SAMPLER_MIN_BLOCKS = 3;
-constexpr unsigned GROUP = 8;  // entries per staged write: one 32-byte sector
+constexpr unsigned GROUP = 8;  // entries per whole-sector store of a capped run: one 32-byte sector
 
 enum { MODE_COUNT = 0, MODE_STAGE = 1, MODE_EMIT = 2 };
 
@@ -163,8 +164,8 @@ template <int MODE, bool WF, typename E>
 __device__ __forceinline__ RunEnd capped_run(const typename Wt<WF>::w_t* __restrict__ W, typename Wt<WF>::w_t wu,
                                           typename Wt<WF>::q_t S, unsigned target, unsigned end, unsigned u,
                                           unsigned seg, unsigned key0, unsigned key1, unsigned* pool,
-                                          unsigned long long sbase, unsigned ssize, int* overflow, unsigned* sg,
-                                          E* edges, long long capacity) {
+                                          unsigned long long sbase, unsigned ssize, int* overflow, E* edges,
+                                          long long capacity) {
   using T = Wt<WF>;
   unsigned lo = target + 1, hi = end;
   while (lo < hi) {
@@ -184,7 +185,7 @@ __device__ __forceinline__ RunEnd capped_run(const typename Wt<WF>::w_t* __restr
       dst[0] = make_uint4(v, v + 1, v + 2, v + 3);
       dst[1] = make_uint4(v + 4, v + 5, v + 6, v + 7);
     }
-    for (unsigned e = 0; g + e < m; ++e) sg[e * SAMPLER_THREADS] = target + g + e;  // the open group
+    for (; g < m; ++g) pool[sbase + g] = target + g;
     if (L > ssize) atomicExch(overflow, 1);  // the item outgrew its slot: EMIT regenerates it
   }
   if (MODE == MODE_EMIT) {
@@ -283,7 +284,6 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
   const w_t* w_l = nullptr;
   q_t S_l = 0;
   Keys<SINGLE> keys{};
-  __shared__ unsigned sgrp[MODE == MODE_STAGE ? GROUP : 1][SAMPLER_THREADS];  // staging group, [entry][thread]
   unsigned n_iter = 0;
   int cur_task = -1;  // the task the warp took last (per-task clock)
   const bool clock_tasks = MODE != MODE_EMIT && P.task_ns != nullptr;
@@ -462,22 +462,9 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
       } else {
         const long long item = s_item[threadIdx.x];
         counts[item] = (int)k;
-        if (MODE == MODE_STAGE) {
-          if (k <= ssize) {
-            // the item's last partial group, written as a whole sector (the slot is a
-            // multiple of 8 entries, so the group lies inside it; entries past k are
-            // never read): no read-modify-write of a partial sector, no per-entry loop
-            if (k & (GROUP - 1)) {
-              uint4* dst = (uint4*)(P.pool + sbase + (k & ~(GROUP - 1)));
-              dst[0] = make_uint4(sgrp[0][threadIdx.x], sgrp[1][threadIdx.x], sgrp[2][threadIdx.x],
-                                  sgrp[3][threadIdx.x]);
-              dst[1] = make_uint4(sgrp[4][threadIdx.x], sgrp[5][threadIdx.x], sgrp[6][threadIdx.x],
-                                  sgrp[7][threadIdx.x]);
-            }
-          } else {  // remember it for the regeneration pass
-            unsigned idx = atomicAdd(P.ovf_count, 1u);
-            if (idx < P.ovf_cap) P.ovf_list[idx] = item;
-          }
+        if (MODE == MODE_STAGE && k > ssize) {  // remember it for the regeneration pass
+          unsigned idx = atomicAdd(P.ovf_count, 1u);
+          if (idx < P.ovf_cap) P.ovf_list[idx] = item;
         }
       }
       have = false;
@@ -582,15 +569,7 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
           }
           if (MODE == MODE_STAGE) {
             if (k < ssize) {
-              unsigned e8 = k & (GROUP - 1);
-              sgrp[e8][threadIdx.x] = target;
-              if (e8 == GROUP - 1) {
-                uint4* dst = (uint4*)(P.pool + sbase + (k & ~(GROUP - 1)));
-                dst[0] = make_uint4(sgrp[0][threadIdx.x], sgrp[1][threadIdx.x], sgrp[2][threadIdx.x],
-                                    sgrp[3][threadIdx.x]);
-                dst[1] = make_uint4(sgrp[4][threadIdx.x], sgrp[5][threadIdx.x], sgrp[6][threadIdx.x],
-                                    sgrp[7][threadIdx.x]);
-              }
+              P.pool[sbase + k] = target;
             } else if (k == ssize) {
               atomicExch(P.overflow, 1);  // the item outgrew its slot: EMIT regenerates it
             }
@@ -626,11 +605,9 @@ __global__ void __launch_bounds__(SAMPLER_THREADS, SAMPLER_MIN_BLOCKS)
         }
       }
       if (fresh && Qt == S && Qt != 0) {  // a capped run from the first position (S = 0: no edge)
-        unsigned* sg = nullptr;
-        if (MODE == MODE_STAGE) sg = &sgrp[0][threadIdx.x];
         const unsigned key0 = SINGLE ? G1.key0 : P.graphs[gi_l].key0, key1 = SINGLE ? G1.key1 : P.graphs[gi_l].key1;
         const RunEnd r = capped_run<MODE, WF, E>(W, wu, S, target, end, u, seg, key0, key1, P.pool, sbase, ssize,
-                                                 P.overflow, sg, edges, capacity);
+                                                 P.overflow, edges, capacity);
         k = r.L;  // its positions' draws are consumed: the next draw is number L
         t = r.L;
         n_iter += r.L;
