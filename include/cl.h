@@ -143,7 +143,8 @@ size_t cl_plan_scratch_bytes(int32_t G);
  * heavy rows and the item space.  SYNCHRONIZING (reads the results back).
  * graphs: host array of G descriptors (copied; the device weight arrays must
  * stay alive and unchanged for the plan's lifetime).  d_scratch: at least
- * cl_plan_scratch_bytes(G) bytes, free again when the call returns.
+ * cl_plan_scratch_bytes(G) bytes, 256-byte aligned (as cudaMalloc returns;
+ * otherwise CL_ERR_INVALID_ARG), free again when the call returns.
  * Errors: CL_ERR_INVALID_ARG, CL_ERR_RANGE, CL_ERR_UNSORTED, CL_ERR_NONFINITE
  * (the first failing graph's status; per-graph status via cl_plan_graph_info),
  * CL_ERR_WORKSPACE, CL_ERR_CUDA.  On error *out is NULL. */
@@ -160,8 +161,10 @@ cl_status cl_plan_workspace_bytes(const cl_plan* plan, size_t* bytes);
  * C = inclusive prefix of c (Calc-Cost of Algorithm 2 as a device-wide scan),
  * task t starts at the first item with C >= t * Zbar, Zbar = C_total / tasks
  * (Eq. 3; found as the items where floor(C / Zbar) changes, the rule of
- * Find-Boundaries).  Asynchronous; capturable in a CUDA graph.  d_ws must stay
- * reserved for the plan until cl_plan_destroy.  Tasks only schedule work: the
+ * Find-Boundaries).  Asynchronous; capturable in a CUDA graph.  d_ws: at least
+ * cl_plan_workspace_bytes bytes (else CL_ERR_WORKSPACE), 256-byte aligned (as
+ * cudaMalloc returns; else CL_ERR_INVALID_ARG), reserved for the plan until
+ * cl_plan_destroy.  Tasks only schedule work: the
  * output does not depend on them. */
 cl_status cl_plan_build(cl_plan* plan, void* d_ws, size_t ws_bytes, cl_stream_t stream);
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <limits>
 #include <new>
@@ -242,6 +243,7 @@ cl_status cl_plan_create(const cl_graph* graphs, int32_t G, const cl_tuning* tun
   const bool f64 = wtype == CL_W_F64;
   ScratchLayout SL = scratch_layout(d_scratch, G, f64);
   if (!d_scratch || scratch_bytes < SL.bytes) return CL_ERR_WORKSPACE;
+  if (((uintptr_t)d_scratch & (ALIGN - 1)) != 0) return CL_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
 
   cl_plan* p = new (std::nothrow) cl_plan();
@@ -426,6 +428,9 @@ cl_status cl_plan_build(cl_plan* p, void* d_ws, size_t ws_bytes, cl_stream_t str
   if (!p) return CL_ERR_INVALID_ARG;
   WsLayout L = ws_layout(d_ws, p);
   if (!d_ws || ws_bytes < L.bytes) return CL_ERR_WORKSPACE;
+  // every array carved from it keeps the base's alignment: the staging pool needs its
+  // 32-byte slot boundaries for the sampler's 16-byte stores and the copy's 16-byte chunks
+  if (((uintptr_t)d_ws & (ALIGN - 1)) != 0) return CL_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   p->ws_bytes = ws_bytes;
   p->d_graphs = L.graphs;

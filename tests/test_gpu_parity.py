@@ -168,6 +168,31 @@ def test_validation_errors(bad, code):
     assert ei.value.status == code
 
 
+def test_misaligned_scratch_and_workspace_rejected():
+    """cl_plan_create and cl_plan_build take 256-byte aligned device memory (the staging
+    pool's 32-byte slot boundaries depend on it); an offset pointer is refused before any
+    launch, and the aligned call that follows succeeds."""
+    P = lib()
+    w = cuda(np.array([9, 7, 7, 4, 2, 1], dtype=np.int32))
+    g = [P.cl_graph(6, P.CL_W_I32, w.data_ptr(), 5, P.HEAVY_W_DEFAULT)]
+    sb = P.cl_plan_scratch_bytes(1)
+    scratch = torch.empty(sb + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(P.ClError) as ei:
+        P.cl_plan_create(g, None, scratch.data_ptr() + 16, sb)
+    assert ei.value.status == P.CL_ERR_INVALID_ARG
+    plan = P.cl_plan_create(g, None, scratch, sb)
+    try:
+        wb = P.cl_plan_workspace_bytes(plan)
+        ws = torch.empty(wb + 512, dtype=torch.uint8, device="cuda")
+        with pytest.raises(P.ClError) as ei:
+            P.cl_plan_build(plan, ws.data_ptr() + 32, wb)
+        assert ei.value.status == P.CL_ERR_INVALID_ARG
+        P.cl_plan_build(plan, ws, wb)
+        torch.cuda.synchronize()
+    finally:
+        P.cl_plan_destroy(plan)
+
+
 def test_empty_and_trivial_graphs():
     for n in (0, 1, 2, 3):
         w = (np.arange(n, 0, -1) * 3).astype(np.int32)
