@@ -6,7 +6,7 @@ from __future__ import annotations
 
 import torch
 
-from . import (CL_E_I32, CL_E_I64, CL_W_F64, CL_W_I32, HEAVY_W_DEFAULT, cl_count, cl_emit, cl_generate,
+from . import (CL_E_I32, CL_W_F64, CL_W_I32, HEAVY_W_DEFAULT, cl_count, cl_emit, cl_generate,
                cl_generate_batch, cl_generate_host, cl_generate_stream,
                cl_graph, cl_plan_build, cl_plan_create, cl_plan_destroy, cl_plan_graph_info, cl_plan_items,
                cl_plan_scratch_bytes, cl_plan_workspace_bytes, cl_scan, cl_stats, cl_tuning)

@@ -9,7 +9,6 @@
 * Capped expected degree and its adjoint against O(n^2) brute force and
   central finite differences.
 """
-import math
 
 import numpy as np
 

@@ -9,7 +9,6 @@ the grid points adjacent to (1-p)^k, where x lies within ~2^-53 of an integer.
 import math
 
 import numpy as np
-import pytest
 
 import oracle
 

@@ -5,7 +5,6 @@ its own graph; a rank that raises ends the job without hanging the other."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 import bench
