@@ -51,7 +51,6 @@ def test_host_side_argument_checks(L):
     sb = L.cl_plan_scratch_bytes(1)
     assert L.cl_plan_create(g, 1, None, ctypes.c_void_p(0x10000010), sb, None, ctypes.byref(out)) == 1
     assert out.value is None
-    assert L.cl_plan_build(None, ctypes.c_void_p(0x10000010), 1 << 20, None) == 1
     assert L.cl_diag_skip(None, None, None, None, -1, None, None, None) == 1
     m = ctypes.c_int64(5)
     assert L.cl_generate_host(None, 0, None, 0, None, None, None, 0, 0, ctypes.byref(m), None) == 1
